@@ -253,7 +253,8 @@ int orc_su2_heatbath(double alpha, uint64_t seed, uint32_t link_id, uint32_t hb_
     } else {
       /* Creutz: b0 from e^{alpha b0} on [-1,1] by inversion, accepted with sqrt(1-b0^2). */
       double e = -expm1(-2.0 * alpha); /* 1 - e^{-2 alpha} */
-      double x = 1.0 + log1p(-r[0] * e) / alpha;
+      /* at alpha = 0 (beta = 0) the inversion is 0/0: take its limit 1 - 2 r */
+      double x = alpha > 0.0 ? 1.0 + log1p(-r[0] * e) / alpha : 1.0 - 2.0 * r[0];
       if (r[1] * r[1] <= 1.0 - x * x) {
         b0 = x;
         used = attempt + 1;

@@ -78,7 +78,7 @@ def _b0_cdf(alpha):
     return lambda q: np.interp(q, x, c)
 
 
-@pytest.mark.parametrize("alpha", [0.2, 1.0, 1.49, 1.5, 4.0, 12.0])
+@pytest.mark.parametrize("alpha", [0.0, 0.2, 1.0, 1.49, 1.5, 4.0, 12.0])
 def test_su2_heatbath_element_distribution(alpha):
     """b0 follows sqrt(1-b0^2) e^{alpha b0} (KS test, both samplers, each side
     of the switch) with mean I_2(alpha)/I_1(alpha); the vector part is
@@ -91,7 +91,7 @@ def test_su2_heatbath_element_distribution(alpha):
     assert np.abs((b ** 2).sum(axis=1) - 1).max() < 1e-13
     ks = stats.kstest(b[:, 0], _b0_cdf(alpha))
     assert ks.pvalue > 1e-3
-    mean = special.iv(2, alpha) / special.iv(1, alpha)
+    mean = special.iv(2, alpha) / special.iv(1, alpha) if alpha > 0 else 0.0
     assert abs(b[:, 0].mean() - mean) < 5 * b[:, 0].std() / np.sqrt(n)
     vec = b[:, 1:] / np.linalg.norm(b[:, 1:], axis=1, keepdims=True)
     assert np.abs(vec.mean(axis=0)).max() < 5 / np.sqrt(3 * n)
@@ -239,3 +239,15 @@ def test_time_slab_passes_compose_to_a_full_pass():
     orc.update_pass(B, 2.3, orc.HEATBATH, 1, 0, 0, 5, t_begin=0, t_end=2)
     orc.update_pass(B, 2.3, orc.HEATBATH, 1, 0, 0, 5, t_begin=2, t_end=6)
     assert np.array_equal(A, B)
+
+
+def test_beta_zero_heatbath_is_haar():
+    """beta = 0: the heatbath draws every link from the Haar measure whatever the
+    staple, so E Tr U = 0 and E|Tr U|^2 = 1."""
+    U = orc.init(3, (4, 4, 4, 4), hot=False, seed=1)
+    orc.sweep(U, 0.0, 1, 0, False, seed=9, hb_step0=0)
+    m = U.reshape(-1, 3, 3)
+    tr = np.trace(m, axis1=1, axis2=2)
+    n = len(tr)
+    assert abs(tr.mean()) < 5 / np.sqrt(n)
+    assert abs((np.abs(tr) ** 2).mean() - 1) < 5 * np.sqrt(2.0 / n)
