@@ -1,0 +1,420 @@
+#!/usr/bin/env python3
+"""Benchmark of the SU(Nc) chessboard link sweep on GB300.
+
+Workload (the configuration the %-of-HBM metric is quoted on): SU(3) on a
+48^3 x 96 lattice, beta = 6.2, cold start, sweeps of 1 heatbath + 5
+overrelaxation steps (each step = 8 chessboard passes), FP32 links in two-row
+(12-real) storage, FP64 reunitarization, plaquette and Polyakov loop measured
+after every sweep.  One benchmark step = one such sweep (the whole hot path).
+
+  value      link updates/s, device-resident lattice (2.0 GB, larger than L2),
+             CUDA events on the lattice's stream, max over ranks
+  e2e        the same metric through the C ABI with host buffers: every step
+             imports the configuration from pinned host memory, sweeps,
+             reads the observables and exports the configuration back
+  roofline   the dominant kernel (overrelaxation pass): algorithmic bytes
+             (8 link reads + 1 link write per update) / measured launch time
+  cpu_baseline  the FP64 CPU oracle on a bounded sample of the same workload
+
+--impl reference times the CPU oracle alone on the same workload and metric.
+Multi-GPU: independent replicas (one lattice per rank), weak scaling.
+"""
+import argparse
+import hashlib
+import glob
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NC, DIMS, BETA = 3, (48, 48, 48, 96), 6.2
+N_HB, N_OR = 1, 5
+METRIC = "link updates/s"
+WORKLOAD_NAME = "SU(3) 48^3x96 beta=6.2 cold start, sweeps of 1 heatbath + 5 overrelaxation, FP32 links"
+
+
+def volume(d):
+    return d[0] * d[1] * d[2] * d[3]
+
+
+def updates_per_sweep():
+    return (N_HB + N_OR) * 4 * volume(DIMS)
+
+
+def source_digest():
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1112_4533_gb300", "csrc", "*"))):
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel_tag):
+    """dram bytes per launch from a committed ncu summary, if it was taken on the current sources."""
+    for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        text = open(path).read()
+        m_k = re.search(r"^roofline_kernel:\s*(\S+)", text, re.M)
+        m_t = re.search(r"^traffic_bytes_per_launch:\s*([0-9.eE+]+)", text, re.M)
+        m_d = re.search(r"^source_digest:\s*(\S+)", text, re.M)
+        if m_k and m_t and m_d and m_k.group(1) == kernel_tag:
+            if m_d.group(1) == source_digest():
+                return float(m_t.group(1))
+            return None
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_selector(local):
+    """nvidia-smi -i argument for this process's GPU (UUID, which ignores CUDA_VISIBLE_DEVICES remapping)."""
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(local).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(local)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------- CPU oracle ----
+
+def oracle_sample(target_seconds=12.0, threads=None, max_slices=24):
+    """Time the FP64 CPU oracle on a bounded sample of the workload: heatbath and
+    overrelaxation passes over the first time slices of the cold 48^3 x 96
+    lattice, each kind repeated over (direction, parity) for about half of
+    target_seconds, rates combined 1:5 as in a sweep.  Returns (updates/s, cores, desc)."""
+    import numpy as np
+    import oracle as orc
+
+    cores = orc.set_threads(threads or os.cpu_count() or 1)
+    nx, ny, nz, nt = DIMS
+    n_slab = max(1, min(max_slices, nt - 2))
+    U = np.zeros((4, nt, nz, ny, nx, NC, NC), dtype=np.complex128)  # pages touched lazily
+    for t in list(range(0, n_slab + 1)) + [nt - 1]:  # cold start on the slices the slab reads
+        for a in range(NC):
+            U[:, t, :, :, :, a, a] = 1.0
+    per_pass = nx * ny * nz // 2 * n_slab
+
+    def rate(mode, budget):
+        n, t_used, k = 0, 0.0, 0
+        while t_used < budget or k == 0:
+            mu, par = (k // 2) % 4, k % 2
+            t0 = time.perf_counter()
+            orc.update_pass(U, BETA, mode, mu, par, 0, 1, 0, n_slab)
+            t_used += time.perf_counter() - t0
+            n += per_pass
+            k += 1
+        return n / t_used, n, t_used
+
+    r_hb, n_hb, t_hb = rate(orc.HEATBATH, target_seconds / 2)
+    r_or, n_or, t_or = rate(orc.OVERRELAX, target_seconds / 2)
+    r = (N_HB + N_OR) / (N_HB / r_hb + N_OR / r_or)
+    desc = (f"heatbath and overrelaxation passes over time slices [0,{n_slab}) of the cold 48^3x96 "
+            f"lattice ({per_pass} link updates per pass): {n_hb} heatbath updates in {t_hb:.1f} s, "
+            f"{n_or} overrelaxation updates in {t_or:.1f} s, rates combined 1:5 as in a sweep")
+    return r, cores, desc
+
+
+# ---------------------------------------------------------------- GPU arm ----
+
+def dist_init(n_gpus):
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def time_kernel(L, reps):
+    """Average duration of one overrelaxation pass, CUDA events on the lattice's stream."""
+    import torch
+    import paper_1112_4533_gb300 as sun
+    evs = []
+    for r in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        mu, par = (r // 2) % 4, r % 2
+        a.record(L.stream)
+        L.update_pass(sun.OVERRELAX, mu, par)
+        b.record(L.stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs) / reps
+
+
+def run_sweeps(L, steps):
+    import torch
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(L.stream)
+    plaq, poly = L.run(steps, N_HB, N_OR)
+    b.record(L.stream)
+    b.synchronize()
+    return a.elapsed_time(b), plaq, poly
+
+
+def gpu_arm(args):
+    import numpy as np
+    import torch
+    import paper_1112_4533_gb300 as sun
+
+    rank, world, local = dist_init(args.gpus)
+    K, W = args.steps, args.warmup
+    V = volume(DIMS)
+    hbm_peak, peak_kind = measured_peaks()
+
+    # ---- headline: FP32, two-row storage
+    L = sun.Lattice(NC, DIMS, BETA, hot_start=False, seed=1 + rank, precision=32, storage=args.storage)
+    L.run(W, N_HB, N_OR)
+    barrier(world)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(gpu_selector(local))
+    sampler.start()
+    ms, plaq, poly = run_sweeps(L, K)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    barrier(world)
+    ms_max = allreduce_max(ms, world)
+    value = updates_per_sweep() * K * world / (ms_max / 1e3)
+
+    # ---- dominant kernel, timed alone (events around each launch)
+    k_ms = time_kernel(L, 32)
+    link_bytes = L.link_bytes
+    alg_bytes = (V // 2) * 9 * link_bytes
+    achieved = alg_bytes / (k_ms / 1e3) / 1e9
+    kernel_tag = f"or_pass_su3_{args.storage}real_fp32_48x48x48x96"
+    traffic = profiled_traffic(kernel_tag)
+
+    # ---- FP32 full (18-real) storage, for the storage comparison
+    variants = {}
+    if not args.no_variants:
+        alt = 18 if args.storage == 12 else 12
+        L.close()
+        del L
+        torch.cuda.empty_cache()
+        L2 = sun.Lattice(NC, DIMS, BETA, hot_start=False, seed=1 + rank, precision=32, storage=alt)
+        L2.run(max(1, W // 2), N_HB, N_OR)
+        ms2, _, _ = run_sweeps(L2, max(2, K // 2))
+        k2 = time_kernel(L2, 16)
+        variants[f"fp32_{alt}real"] = {
+            "value": updates_per_sweep() * max(2, K // 2) / (ms2 / 1e3), "unit": METRIC,
+            "ms_per_step": ms2 / max(2, K // 2), "or_pass_ms": k2,
+            "or_pass_gbs": (V // 2) * 9 * L2.link_bytes / (k2 / 1e3) / 1e9}
+        L2.close()
+        del L2
+        torch.cuda.empty_cache()
+        L = sun.Lattice(NC, DIMS, BETA, hot_start=False, seed=1 + rank, precision=32, storage=args.storage)
+
+    # ---- end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        n_doubles = 8 * NC * NC * V
+        host_a = torch.empty(n_doubles, dtype=torch.float64).pin_memory()
+        host_b = torch.empty(n_doubles, dtype=torch.float64).pin_memory()
+        L.export_links_raw(host_a.data_ptr(), n_doubles)
+        ke = max(2, min(K, args.e2e_steps))
+        for _ in range(1):
+            L.import_links_raw(host_a.data_ptr(), n_doubles)
+            L.run(1, N_HB, N_OR)
+            L.export_links_raw(host_b.data_ptr(), n_doubles)
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for s in range(ke):
+            src, dst = (host_a, host_b) if s % 2 == 0 else (host_b, host_a)
+            L.import_links_raw(src.data_ptr(), n_doubles)
+            L.run(1, N_HB, N_OR)
+            L.export_links_raw(dst.data_ptr(), n_doubles)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        dt = allreduce_max(dt, world)
+        e2e = {"value": updates_per_sweep() * ke * world / dt, "unit": METRIC,
+               "h2d_bytes_per_step": n_doubles * 8, "d2h_bytes_per_step": n_doubles * 8 + 3 * 8,
+               "steps": ke, "ms_per_step": dt / ke * 1e3,
+               "path": "sun_import_links + sun_run(1 sweep, observables to host) + sun_export_links, "
+                       "canonical FP64 links in pinned host memory"}
+        del host_a, host_b
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, cores, desc = oracle_sample(args.cpu_seconds)
+        cpu = {"value": rate, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": desc}
+
+    L.close()
+    launches_per_sweep = (N_HB + N_OR) * 8 + 4  # passes, reunitarization, plaquette, Polyakov, counter
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": METRIC,
+        "n_gpus": world,
+        "steps": K,
+        "warmup": W,
+        "ms_per_step": ms_max / K,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (cold start, Philox seed 1 + rank)",
+        "config": {"workload": WORKLOAD_NAME, "nc": NC, "dims": list(DIMS), "beta": BETA,
+                   "n_heatbath": N_HB, "n_overrelax": N_OR, "storage_reals": args.storage,
+                   "reunitarize": "FP64 every sweep", "observables": "FP64 plaquette + Polyakov every sweep",
+                   "link_updates_per_step": updates_per_sweep(),
+                   "l2": "lattice (2.0 GB) larger than L2, no flush", "parallelism": f"replicas x{world}"},
+        "hbm_gbs_effective": updates_per_sweep() * 9 * link_bytes / (ms_max / K / 1e3) / 1e9,
+        "plaquette_last": float(plaq[-1]),
+        "polyakov_last": [float(poly[-1].real), float(poly[-1].imag)],
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": traffic,
+                     "kernel": "update_pass_mat<float,3,two-row,overrelax>",
+                     "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": k_ms,
+                     "peak_kind": peak_kind + " (hbm_gbs, copy kernel)"},
+        "variants": variants,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "gpu_launches": launches_per_sweep * K,
+    }
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    K, W = args.steps, args.warmup
+    per = max(2.0, min(20.0, 150.0 / max(1, K + W)))
+    for _ in range(W):
+        oracle_sample(per / 4)
+    rates, cores, desc = [], 1, ""
+    t0 = time.perf_counter()
+    for _ in range(K):
+        r, cores, desc = oracle_sample(per)
+        rates.append(r)
+    dt = time.perf_counter() - t0
+    value = sum(rates) / len(rates)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 0, "steps": K,
+           "warmup": W, "ms_per_step": dt / K * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic (cold start)",
+           "config": {"workload": WORKLOAD_NAME, "nc": NC, "dims": list(DIMS), "beta": BETA,
+                      "n_heatbath": N_HB, "n_overrelax": N_OR},
+           "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": desc},
+           "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--storage", type=int, default=12, choices=[12, 18])
+    ap.add_argument("--e2e-steps", type=int, default=8)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,168 @@
+/*
+ * sun.h -- C ABI of the GB300 (sm_103a) SU(Nc) pure-gauge link-sweep library.
+ *
+ * The operations follow Cardoso & Bicudo, "Generating SU(Nc) pure gauge lattice
+ * QCD configurations on GPUs with CUDA" (arXiv:1112.4533):
+ *   Sec. 2, Eqs. 3-4    Wilson action and plaquette
+ *   Sec. 2, Eq. 9       six-plaquette staple
+ *   Sec. 2, Eqs. 10-15  SU(2) heatbath and the Cabibbo-Marinari pseudo-heatbath
+ *   Sec. 2, Eq. 17      overrelaxation
+ *   Sec. 2 (end)        re-unitarization
+ *   Sec. 3              hot/cold start, the chessboard (direction x even/odd)
+ *                       schedule of eight passes per step, 12-real SU(3) storage
+ *
+ * Conventions shared by every entry point
+ *  - Every call returns a sun_status and never aborts the process.  On failure
+ *    sun_last_error() returns a message for the calling thread.
+ *  - Lattice extents dims = {Nx, Ny, Nz, Nt} (mu = 0,1,2,3 = x,y,z,t), periodic,
+ *    each even and >= 2 (the even/odd colouring must close over the boundary),
+ *    and 4*Nx*Ny*Nz*Nt < 2^32 (links are numbered with 32 bits for the RNG).
+ *  - Canonical link order (host interchange format, FP64, independent of the
+ *    storage format and precision): double[ ((mu*V + lex)*Nc + row)*Nc + col ][2]
+ *    with lex = x + Nx*(y + Ny*(z + Nz*t)), V = Nx*Ny*Nz*Nt; i.e. 8*Nc*Nc*V doubles.
+ *  - Device work is enqueued on the lattice's CUDA stream and is asynchronous
+ *    unless stated otherwise ("syncs").  Host pointers passed in may be pageable
+ *    or pinned.
+ *  - Random numbers: Philox4x32-10 keyed by the 64-bit seed, counter =
+ *    (mu*V + lex, heatbath step, (subgroup << 16) | attempt, 1).  (seed, heatbath
+ *    step) is the whole random state of a lattice.
+ */
+#ifndef SUN_H
+#define SUN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SUN_ABI_VERSION 1
+
+typedef struct sun_lattice sun_lattice; /* opaque, owned by the library */
+
+typedef enum {
+  SUN_OK = 0,
+  SUN_ERR_ARG = 1,         /* an argument is out of range or inconsistent           */
+  SUN_ERR_OOM = 2,         /* device memory unavailable or caller buffer too small  */
+  SUN_ERR_CUDA = 3,        /* a CUDA runtime call failed                            */
+  SUN_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up                    */
+  SUN_ERR_UNSUPPORTED = 5, /* (Nc, storage, precision) combination not built        */
+  SUN_ERR_STATE = 6        /* call not valid in the object's current state          */
+} sun_status;
+
+/* update modes of sun_update_pass */
+enum { SUN_HEATBATH = 0, SUN_OVERRELAX = 1 };
+
+/*
+ * Options of a lattice.  Call sun_options_init() first, then change fields.
+ *  precision     32 or 64: link storage and update arithmetic (default 32).
+ *                Re-unitarization and the accumulation of the plaquette and the
+ *                Polyakov loop are FP64 in both cases.
+ *  storage       reals stored per link; 0 picks the default.  Nc=2: 4 (a0..a3 of
+ *                Eq. 6, default) or 8 (full 2x2).  Nc=3: 12 (two rows, third row
+ *                rebuilt as conj(row0 x row1), Sec. 3, default) or 18 (full).
+ *                Nc>=4: 2*Nc*Nc.
+ *  reunit_every  sun_sweep re-unitarizes after every reunit_every-th sweep; 0 = never
+ *                (default 1).
+ *  block_threads CUDA block size of the update passes, 0 = default (128).
+ *  stream        cudaStream_t the lattice enqueues on; NULL = a stream the library
+ *                creates and owns.
+ *  device_buf    optional caller-owned device memory of device_buf_bytes bytes
+ *                (>= sun_footprint_bytes) holding all device state of the lattice;
+ *                it must be 256-byte aligned and outlive the lattice.  NULL = the
+ *                library allocates (cudaMalloc) and frees.
+ *  use_graphs    sun_run captures one sweep as a CUDA graph and replays it (default 1).
+ */
+typedef struct {
+  int precision;
+  int storage;
+  int reunit_every;
+  int block_threads;
+  void* stream;
+  void* device_buf;
+  size_t device_buf_bytes;
+  int use_graphs;
+} sun_options;
+
+int sun_abi_version(void);
+void sun_options_init(sun_options* opt);
+const char* sun_status_string(sun_status s);
+const char* sun_last_error(void); /* thread-local, "" when none */
+
+/* Bytes of device memory a lattice needs (links, reduction scratch, observable
+ * history, import/export staging).  0 if the arguments are invalid. */
+size_t sun_footprint_bytes(int nc, const int dims[4], const sun_options* opt);
+
+/* Create a lattice and initialise it (Sec. 3): cold start = every link the
+ * identity; hot start = every link Haar-random in SU(Nc) (complex Gaussian matrix,
+ * Gram-Schmidt, determinant phase), drawn with Philox counter (mu*V+lex, 0, k, 2).
+ * beta = 2 Nc / g^2 (Eq. 3) must be >= 0.  The heatbath step counter starts at 0.
+ * On success *out owns the lattice; on failure *out is NULL. */
+sun_status sun_lattice_create(sun_lattice** out, int nc, const int dims[4], double beta,
+                              int hot_start, uint64_t seed, const sun_options* opt);
+void sun_lattice_destroy(sun_lattice* lat); /* syncs; NULL is a no-op */
+
+/* One chessboard pass (Sec. 3): every link U_mu(x) with (x+y+z+t) % 2 == parity is
+ * updated from its staple (Eq. 9) by the pseudo-heatbath (mode SUN_HEATBATH,
+ * Eqs. 10-15, Kennedy-Pendleton/Creutz SU(2) subgroup draws, at most 64 attempts
+ * per subgroup, using the current heatbath step counter) or by overrelaxation
+ * (SUN_OVERRELAX, Eq. 17 per subgroup).  Does not advance the step counter. */
+sun_status sun_update_pass(sun_lattice* lat, int mode, int mu, int parity);
+
+/* One sweep: n_heatbath heatbath steps then n_overrelax overrelaxation steps, a step
+ * being the eight passes mu = 0..3 x (even, odd); then re-unitarization if this is a
+ * reunit_every-th sweep.  Heatbath step s of the sweep uses counter value c + s,
+ * and the counter advances by n_heatbath. */
+sun_status sun_sweep(sun_lattice* lat, int n_heatbath, int n_overrelax);
+
+/* n_sweeps sweeps as sun_sweep, each followed by the plaquette (if plaq_hist) and
+ * the Polyakov loop (if poly_hist, re/im pairs) measured on the device; the
+ * histories (n_sweeps and 2*n_sweeps doubles, host memory) are copied out at the
+ * end.  With use_graphs, one sweep is captured as a CUDA graph and replayed.  Syncs. */
+sun_status sun_run(sun_lattice* lat, int n_sweeps, int n_heatbath, int n_overrelax,
+                   double* plaq_hist, double* poly_hist);
+
+/* Re-unitarize every link in FP64 (Sec. 2): Nc=2 normalise the first row and
+ * rebuild the second; Nc=3 Gram-Schmidt rows 0,1 and row 2 = conj(row0 x row1);
+ * Nc>3 Gram-Schmidt all rows, then the last row times conj(det). */
+sun_status sun_reunitarize(sun_lattice* lat);
+
+/* <P> = sum_x sum_{mu<nu} ReTr P_{mu nu}(x) / (6 V Nc) (Eq. 4), products in the
+ * storage precision, accumulated in FP64 with a fixed reduction order.  Syncs. */
+sun_status sun_plaquette(sun_lattice* lat, double* out);
+
+/* Polyakov loop L = sum_{x,y,z} Tr prod_{t=0}^{Nt-1} U_3(x,y,z,t) / (Nc Nx Ny Nz),
+ * accumulated in FP64 (not defined in the paper; the usual order-parameter
+ * definition).  Syncs. */
+sun_status sun_polyakov_loop(sun_lattice* lat, double* re, double* im);
+
+/* Copy all links to / from host memory in canonical order (n_doubles must equal
+ * 8*Nc*Nc*V).  Export rebuilds the third row of 12-real storage; import of a
+ * 12-real lattice keeps rows 0 and 1 only.  Both sync. */
+sun_status sun_export_links(sun_lattice* lat, double* host, size_t n_doubles);
+sun_status sun_import_links(sun_lattice* lat, const double* host, size_t n_doubles);
+
+/* Random state: the heatbath step counter (the seed is fixed at creation). */
+sun_status sun_get_heatbath_step(sun_lattice* lat, uint64_t* step); /* syncs */
+sun_status sun_set_heatbath_step(sun_lattice* lat, uint64_t step);
+sun_status sun_set_beta(sun_lattice* lat, double beta);
+sun_status sun_synchronize(sun_lattice* lat);
+
+typedef struct {
+  int nc, precision, storage, reserved;
+  int dims[4];
+  double beta;
+  uint64_t seed;
+  size_t link_bytes;     /* bytes of one stored link                     */
+  size_t links_bytes;    /* bytes of all 4V links                        */
+  size_t footprint;      /* device bytes held by the lattice             */
+  void* links;           /* device address of the link storage           */
+  void* stream;          /* cudaStream_t the lattice enqueues on         */
+} sun_lattice_info;
+sun_status sun_get_info(const sun_lattice* lat, sun_lattice_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SUN_H */

@@ -1,0 +1,571 @@
+// api.cu -- C ABI of the SU(Nc) link-sweep library (declared in include/sun.h).
+//
+// Owns the lattice handle: device memory layout, the chessboard schedule of
+// Sec. 3 of Cardoso & Bicudo (arXiv:1112.4533) -- per step, directions
+// mu = 0..3 each as an even then an odd pass --, CUDA-graph capture of one
+// sweep, deterministic observable reductions and the canonical FP64
+// import/export path.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+
+#include "sun.h"
+#include "sun_runtime.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+sun_status fail(sun_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
+#define SUN_CUDA(call)                                                                             \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess)                                                                         \
+      return fail(SUN_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                  __LINE__);                                                                       \
+  } while (0)
+
+#define SUN_TRY(expr)               \
+  do {                              \
+    sun_status s_ = (expr);         \
+    if (s_ != SUN_OK) return s_;    \
+  } while (0)
+
+constexpr size_t kAlign = 256;
+constexpr size_t kStagingCap = size_t(16) << 20;  // import/export chunk buffer
+constexpr int kHistCap = 1024;                    // sweeps per observable-history chunk
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+const sun::Ops* find_ops(int nc, int storage, int precision) {
+  switch (nc) {
+    case 2: return sun::ops_su2(storage, precision);
+    case 3: return sun::ops_su3(storage, precision);
+    case 4: return sun::ops_su4(storage, precision);
+    case 5: return sun::ops_su5(storage, precision);
+    case 6: return sun::ops_su6(storage, precision);
+    default: return nullptr;
+  }
+}
+
+int default_storage(int nc) { return nc == 2 ? 4 : (nc == 3 ? 12 : 2 * nc * nc); }
+
+sun_status check_dims(const int* dims) {
+  if (!dims) return fail(SUN_ERR_ARG, "dims is NULL");
+  int64_t V = 1;
+  for (int m = 0; m < 4; ++m) {
+    if (dims[m] < 2 || (dims[m] & 1))
+      return fail(SUN_ERR_ARG, "lattice extent dims[%d] = %d must be even and >= 2", m, dims[m]);
+    V *= dims[m];
+    if (V > (int64_t(1) << 30)) break;
+  }
+  if (4 * V >= (int64_t(1) << 32)) return fail(SUN_ERR_ARG, "4 * volume must be < 2^32");
+  return SUN_OK;
+}
+
+struct Plan {
+  size_t links_off, state_off, partials_off, results_off, hist_off, staging_off, total;
+  size_t links_bytes, staging_bytes;
+  int64_t staging_links;
+};
+
+Plan make_plan(int nc, const int* dims, int link_bytes) {
+  Plan p;
+  const int64_t V = int64_t(dims[0]) * dims[1] * dims[2] * dims[3];
+  const size_t canon_link = size_t(2) * nc * nc * sizeof(double);
+  p.links_bytes = size_t(4 * V) * size_t(link_bytes);
+  int64_t sl = int64_t(kStagingCap / canon_link);
+  if (sl < 1) sl = 1;
+  if (sl > 4 * V) sl = 4 * V;
+  p.staging_links = sl;
+  p.staging_bytes = size_t(sl) * canon_link;
+  size_t off = 0;
+  p.links_off = off;
+  off = align_up(off + p.links_bytes, kAlign);
+  p.state_off = off;
+  off = align_up(off + sizeof(sun::DevState), kAlign);
+  p.partials_off = off;
+  off = align_up(off + 4 * sun::kMaxReduceBlocks * sizeof(double), kAlign);
+  p.results_off = off;
+  off = align_up(off + 8 * sizeof(double), kAlign);
+  p.hist_off = off;
+  off = align_up(off + 3 * kHistCap * sizeof(double), kAlign);
+  p.staging_off = off;
+  off = align_up(off + p.staging_bytes, kAlign);
+  p.total = off;
+  return p;
+}
+
+__global__ void bump_kernel(sun::DevState* st, uint32_t hb_steps, uint32_t slots) {
+  st->hb_step += hb_steps;
+  st->slot += slots;
+}
+
+struct GraphKey {
+  int n_hb, n_or, reunit, plaq, poly;
+  bool operator<(const GraphKey& o) const {
+    return std::tie(n_hb, n_or, reunit, plaq, poly) < std::tie(o.n_hb, o.n_or, o.reunit, o.plaq, o.poly);
+  }
+};
+
+}  // namespace
+
+struct sun_lattice {
+  int nc = 0, precision = 0, storage = 0;
+  int dims[4] = {0, 0, 0, 0};
+  double beta = 0.0;
+  uint64_t seed = 0;
+  int reunit_every = 1, block_threads = 128, use_graphs = 1;
+  int device = 0;
+  uint64_t sweeps_done = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaStream_t capture_stream = nullptr;
+  char* base = nullptr;
+  bool own_mem = false;
+  Plan plan{};
+  const sun::Ops* ops = nullptr;
+  sun::Ctx ctx{};
+  double* results = nullptr;
+  double* hist = nullptr;
+  double* staging = nullptr;
+  double* host_results = nullptr;  // pinned, 8 doubles
+  std::map<GraphKey, cudaGraphExec_t> graphs;
+};
+
+namespace {
+
+sun_status set_device(const sun_lattice* L) {
+  SUN_CUDA(cudaSetDevice(L->device));
+  return SUN_OK;
+}
+
+void drop_graphs(sun_lattice* L) {
+  for (auto& kv : L->graphs) cudaGraphExecDestroy(kv.second);
+  L->graphs.clear();
+}
+
+sun::Ctx ctx_on(const sun_lattice* L, cudaStream_t s) {
+  sun::Ctx c = L->ctx;
+  c.stream = s;
+  c.beta = L->beta;
+  return c;
+}
+
+sun_status check_launch(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) return fail(SUN_ERR_CUDA, "launch of %s failed: %s", what, cudaGetErrorString(e));
+  return SUN_OK;
+}
+
+// Enqueue one sweep on stream s.  hist_mode: observables go to the history slot
+// held in device state, which is advanced at the end of the sweep.
+sun_status enqueue_sweep(sun_lattice* L, cudaStream_t s, int n_hb, int n_or, bool reunit, bool plaq,
+                         bool poly, bool hist_mode) {
+  const sun::Ctx c = ctx_on(L, s);
+  for (int step = 0; step < n_hb; ++step)
+    for (int mu = 0; mu < 4; ++mu)
+      for (int p = 0; p < 2; ++p)
+        SUN_TRY(check_launch(L->ops->pass(c, SUN_HEATBATH, mu, p, uint32_t(step)), "heatbath pass"));
+  for (int step = 0; step < n_or; ++step)
+    for (int mu = 0; mu < 4; ++mu)
+      for (int p = 0; p < 2; ++p)
+        SUN_TRY(check_launch(L->ops->pass(c, SUN_OVERRELAX, mu, p, 0u), "overrelaxation pass"));
+  if (reunit) SUN_TRY(check_launch(L->ops->reunit(c), "reunitarization"));
+  const uint32_t* slot = hist_mode ? &L->ctx.state->slot : nullptr;
+  if (plaq) SUN_TRY(check_launch(L->ops->plaquette(c, hist_mode ? L->hist : L->results, slot, kHistCap), "plaquette"));
+  if (poly)
+    SUN_TRY(check_launch(L->ops->polyakov(c, hist_mode ? L->hist + kHistCap : L->results + 2, slot, kHistCap),
+                         "polyakov"));
+  if (n_hb > 0 || hist_mode) {
+    bump_kernel<<<1, 1, 0, s>>>(L->ctx.state, uint32_t(n_hb), hist_mode ? 1u : 0u);
+    SUN_TRY(check_launch(cudaGetLastError(), "step counter"));
+  }
+  return SUN_OK;
+}
+
+bool reunit_due(const sun_lattice* L, uint64_t sweep_index) {
+  return L->reunit_every > 0 && ((sweep_index + 1) % uint64_t(L->reunit_every)) == 0;
+}
+
+sun_status get_graph(sun_lattice* L, const GraphKey& key, cudaGraphExec_t* out) {
+  auto it = L->graphs.find(key);
+  if (it != L->graphs.end()) {
+    *out = it->second;
+    return SUN_OK;
+  }
+  SUN_CUDA(cudaStreamBeginCapture(L->capture_stream, cudaStreamCaptureModeThreadLocal));
+  sun_status st = enqueue_sweep(L, L->capture_stream, key.n_hb, key.n_or, key.reunit != 0, key.plaq != 0,
+                                key.poly != 0, true);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(L->capture_stream, &g);
+  if (st != SUN_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return fail(SUN_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(SUN_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+  L->graphs[key] = exec;
+  *out = exec;
+  return SUN_OK;
+}
+
+sun_status read_results(sun_lattice* L, int count) {
+  SUN_CUDA(cudaMemcpyAsync(L->host_results, L->results, count * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+  SUN_CUDA(cudaStreamSynchronize(L->stream));
+  return SUN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sun_abi_version(void) { return SUN_ABI_VERSION; }
+
+void sun_options_init(sun_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->precision = 32;
+  opt->storage = 0;
+  opt->reunit_every = 1;
+  opt->block_threads = 0;
+  opt->stream = nullptr;
+  opt->device_buf = nullptr;
+  opt->device_buf_bytes = 0;
+  opt->use_graphs = 1;
+}
+
+const char* sun_status_string(sun_status s) {
+  switch (s) {
+    case SUN_OK: return "ok";
+    case SUN_ERR_ARG: return "invalid argument";
+    case SUN_ERR_OOM: return "out of device memory";
+    case SUN_ERR_CUDA: return "CUDA error";
+    case SUN_ERR_TIMEOUT: return "device wait timed out";
+    case SUN_ERR_UNSUPPORTED: return "unsupported combination";
+    case SUN_ERR_STATE: return "invalid state";
+  }
+  return "unknown status";
+}
+
+const char* sun_last_error(void) { return g_last_error.c_str(); }
+
+static sun_status resolve(int nc, const int* dims, const sun_options* opt_in, sun_options* opt, const sun::Ops** ops) {
+  if (opt_in)
+    *opt = *opt_in;
+  else
+    sun_options_init(opt);
+  if (nc < 2) return fail(SUN_ERR_ARG, "nc = %d must be >= 2", nc);
+  SUN_TRY(check_dims(dims));
+  if (opt->precision != 32 && opt->precision != 64)
+    return fail(SUN_ERR_ARG, "precision = %d must be 32 or 64", opt->precision);
+  if (opt->storage == 0) opt->storage = default_storage(nc);
+  if (opt->reunit_every < 0) return fail(SUN_ERR_ARG, "reunit_every must be >= 0");
+  if (opt->block_threads == 0) opt->block_threads = 128;
+  if (opt->block_threads < 32 || opt->block_threads > 256 || (opt->block_threads & 31))
+    return fail(SUN_ERR_ARG, "block_threads = %d must be a multiple of 32 in [32, 256]", opt->block_threads);
+  *ops = find_ops(nc, opt->storage, opt->precision);
+  if (!*ops)
+    return fail(SUN_ERR_UNSUPPORTED, "no kernels for nc = %d, storage = %d, precision = %d (built: nc 2..6)", nc,
+                opt->storage, opt->precision);
+  return SUN_OK;
+}
+
+size_t sun_footprint_bytes(int nc, const int dims[4], const sun_options* opt_in) {
+  sun_options opt;
+  const sun::Ops* ops = nullptr;
+  if (resolve(nc, dims, opt_in, &opt, &ops) != SUN_OK) return 0;
+  return make_plan(nc, dims, ops->link_bytes).total;
+}
+
+sun_status sun_lattice_create(sun_lattice** out, int nc, const int dims[4], double beta, int hot_start,
+                              uint64_t seed, const sun_options* opt_in) {
+  if (!out) return fail(SUN_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  sun_options opt;
+  const sun::Ops* ops = nullptr;
+  SUN_TRY(resolve(nc, dims, opt_in, &opt, &ops));
+  if (!(beta >= 0.0)) return fail(SUN_ERR_ARG, "beta must be >= 0");
+
+  sun_lattice* L = new sun_lattice();
+  L->nc = nc;
+  L->precision = opt.precision;
+  L->storage = opt.storage;
+  for (int m = 0; m < 4; ++m) L->dims[m] = dims[m];
+  L->beta = beta;
+  L->seed = seed;
+  L->reunit_every = opt.reunit_every;
+  L->block_threads = opt.block_threads;
+  L->use_graphs = opt.use_graphs;
+  L->ops = ops;
+  L->plan = make_plan(nc, dims, ops->link_bytes);
+
+  auto cleanup = [&](sun_status s) {
+    sun_lattice_destroy(L);
+    return s;
+  };
+  if (cudaGetDevice(&L->device) != cudaSuccess) return cleanup(fail(SUN_ERR_CUDA, "no CUDA device"));
+  if (opt.device_buf) {
+    if (reinterpret_cast<uintptr_t>(opt.device_buf) % kAlign)
+      return cleanup(fail(SUN_ERR_ARG, "device_buf must be %zu-byte aligned", kAlign));
+    if (opt.device_buf_bytes < L->plan.total)
+      return cleanup(fail(SUN_ERR_OOM, "device_buf holds %zu bytes, lattice needs %zu", opt.device_buf_bytes,
+                          L->plan.total));
+    L->base = static_cast<char*>(opt.device_buf);
+    L->own_mem = false;
+  } else {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, L->plan.total);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return cleanup(fail(SUN_ERR_OOM, "cudaMalloc(%zu) failed: %s", L->plan.total, cudaGetErrorString(e)));
+    }
+    L->base = static_cast<char*>(p);
+    L->own_mem = true;
+  }
+  if (opt.stream) {
+    L->stream = static_cast<cudaStream_t>(opt.stream);
+    L->own_stream = false;
+  } else {
+    if (cudaStreamCreateWithFlags(&L->stream, cudaStreamNonBlocking) != cudaSuccess)
+      return cleanup(fail(SUN_ERR_CUDA, "stream creation failed"));
+    L->own_stream = true;
+  }
+  if (cudaStreamCreateWithFlags(&L->capture_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return cleanup(fail(SUN_ERR_CUDA, "capture stream creation failed"));
+  if (cudaMallocHost(&L->host_results, 8 * sizeof(double)) != cudaSuccess)
+    return cleanup(fail(SUN_ERR_CUDA, "pinned result buffer allocation failed"));
+
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, L->device);
+  sun::Geom g;
+  g.nx = dims[0];
+  g.ny = dims[1];
+  g.nz = dims[2];
+  g.nt = dims[3];
+  g.nxh = dims[0] / 2;
+  g.V = int64_t(dims[0]) * dims[1] * dims[2] * dims[3];
+  g.Vh = g.V / 2;
+  g.stride[0] = 1;
+  g.stride[1] = dims[0];
+  g.stride[2] = int64_t(dims[0]) * dims[1];
+  g.stride[3] = int64_t(dims[0]) * dims[1] * dims[2];
+
+  sun::Ctx& c = L->ctx;
+  c.links = L->base + L->plan.links_off;
+  c.block_bytes = g.Vh * ops->link_bytes;
+  c.g = g;
+  c.beta = beta;
+  c.seed = seed;
+  c.nc = nc;
+  c.state = reinterpret_cast<sun::DevState*>(L->base + L->plan.state_off);
+  c.partials = reinterpret_cast<double*>(L->base + L->plan.partials_off);
+  c.stream = L->stream;
+  c.block_threads = L->block_threads;
+  int rb = 2 * (sms > 0 ? sms : 132);
+  c.reduce_blocks = rb > sun::kMaxReduceBlocks ? sun::kMaxReduceBlocks : rb;
+  L->results = reinterpret_cast<double*>(L->base + L->plan.results_off);
+  L->hist = reinterpret_cast<double*>(L->base + L->plan.hist_off);
+  L->staging = reinterpret_cast<double*>(L->base + L->plan.staging_off);
+
+  if (cudaMemsetAsync(c.state, 0, sizeof(sun::DevState), L->stream) != cudaSuccess)
+    return cleanup(fail(SUN_ERR_CUDA, "state reset failed"));
+  sun_status st = check_launch(ops->init(ctx_on(L, L->stream), hot_start ? 1 : 0), "init");
+  if (st != SUN_OK) return cleanup(st);
+  *out = L;
+  return SUN_OK;
+}
+
+void sun_lattice_destroy(sun_lattice* L) {
+  if (!L) return;
+  cudaSetDevice(L->device);
+  if (L->stream) cudaStreamSynchronize(L->stream);
+  drop_graphs(L);
+  if (L->capture_stream) cudaStreamDestroy(L->capture_stream);
+  if (L->own_stream && L->stream) cudaStreamDestroy(L->stream);
+  if (L->own_mem && L->base) cudaFree(L->base);
+  if (L->host_results) cudaFreeHost(L->host_results);
+  delete L;
+}
+
+sun_status sun_update_pass(sun_lattice* L, int mode, int mu, int parity) {
+  if (!L) return fail(SUN_ERR_ARG, "lattice is NULL");
+  if (mode != SUN_HEATBATH && mode != SUN_OVERRELAX) return fail(SUN_ERR_ARG, "mode must be 0 or 1");
+  if (mu < 0 || mu > 3) return fail(SUN_ERR_ARG, "mu must be in 0..3");
+  if (parity != 0 && parity != 1) return fail(SUN_ERR_ARG, "parity must be 0 or 1");
+  SUN_TRY(set_device(L));
+  return check_launch(L->ops->pass(ctx_on(L, L->stream), mode, mu, parity, 0u), "update pass");
+}
+
+sun_status sun_sweep(sun_lattice* L, int n_hb, int n_or) {
+  if (!L) return fail(SUN_ERR_ARG, "lattice is NULL");
+  if (n_hb < 0 || n_or < 0) return fail(SUN_ERR_ARG, "step counts must be >= 0");
+  SUN_TRY(set_device(L));
+  SUN_TRY(enqueue_sweep(L, L->stream, n_hb, n_or, reunit_due(L, L->sweeps_done), false, false, false));
+  L->sweeps_done++;
+  return SUN_OK;
+}
+
+sun_status sun_run(sun_lattice* L, int n_sweeps, int n_hb, int n_or, double* plaq_hist, double* poly_hist) {
+  if (!L) return fail(SUN_ERR_ARG, "lattice is NULL");
+  if (n_sweeps < 0 || n_hb < 0 || n_or < 0) return fail(SUN_ERR_ARG, "counts must be >= 0");
+  SUN_TRY(set_device(L));
+  const bool plaq = plaq_hist != nullptr, poly = poly_hist != nullptr;
+  for (int done = 0; done < n_sweeps;) {
+    const int chunk = (n_sweeps - done) < kHistCap ? (n_sweeps - done) : kHistCap;
+    SUN_CUDA(cudaMemsetAsync(&L->ctx.state->slot, 0, sizeof(uint32_t), L->stream));
+    for (int k = 0; k < chunk; ++k) {
+      const bool reunit = reunit_due(L, L->sweeps_done);
+      if (L->use_graphs) {
+        cudaGraphExec_t exec = nullptr;
+        SUN_TRY(get_graph(L, GraphKey{n_hb, n_or, reunit ? 1 : 0, plaq ? 1 : 0, poly ? 1 : 0}, &exec));
+        SUN_CUDA(cudaGraphLaunch(exec, L->stream));
+      } else {
+        SUN_TRY(enqueue_sweep(L, L->stream, n_hb, n_or, reunit, plaq, poly, true));
+      }
+      L->sweeps_done++;
+    }
+    if (plaq)
+      SUN_CUDA(cudaMemcpyAsync(plaq_hist + done, L->hist, chunk * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+    if (poly)
+      SUN_CUDA(cudaMemcpyAsync(poly_hist + 2 * done, L->hist + kHistCap, 2 * chunk * sizeof(double),
+                               cudaMemcpyDeviceToHost, L->stream));
+    done += chunk;
+  }
+  SUN_CUDA(cudaStreamSynchronize(L->stream));
+  return SUN_OK;
+}
+
+sun_status sun_reunitarize(sun_lattice* L) {
+  if (!L) return fail(SUN_ERR_ARG, "lattice is NULL");
+  SUN_TRY(set_device(L));
+  return check_launch(L->ops->reunit(ctx_on(L, L->stream)), "reunitarization");
+}
+
+sun_status sun_plaquette(sun_lattice* L, double* out) {
+  if (!L || !out) return fail(SUN_ERR_ARG, "NULL argument");
+  SUN_TRY(set_device(L));
+  SUN_TRY(check_launch(L->ops->plaquette(ctx_on(L, L->stream), L->results, nullptr, 1), "plaquette"));
+  SUN_TRY(read_results(L, 1));
+  *out = L->host_results[0];
+  return SUN_OK;
+}
+
+sun_status sun_polyakov_loop(sun_lattice* L, double* re, double* im) {
+  if (!L || !re || !im) return fail(SUN_ERR_ARG, "NULL argument");
+  SUN_TRY(set_device(L));
+  SUN_TRY(check_launch(L->ops->polyakov(ctx_on(L, L->stream), L->results + 2, nullptr, 1), "polyakov"));
+  SUN_TRY(read_results(L, 4));
+  *re = L->host_results[2];
+  *im = L->host_results[3];
+  return SUN_OK;
+}
+
+static size_t canonical_doubles(const sun_lattice* L) { return size_t(8) * L->nc * L->nc * size_t(L->ctx.g.V); }
+
+sun_status sun_export_links(sun_lattice* L, double* host, size_t n) {
+  if (!L || !host) return fail(SUN_ERR_ARG, "NULL argument");
+  if (n != canonical_doubles(L)) return fail(SUN_ERR_ARG, "host buffer holds %zu doubles, need %zu", n, canonical_doubles(L));
+  SUN_TRY(set_device(L));
+  const sun::Ctx c = ctx_on(L, L->stream);
+  const int64_t total = 4 * L->ctx.g.V, per = 2 * L->nc * L->nc;
+  for (int64_t first = 0; first < total; first += L->plan.staging_links) {
+    const int64_t cnt = (total - first) < L->plan.staging_links ? (total - first) : L->plan.staging_links;
+    SUN_TRY(check_launch(L->ops->export_links(c, L->staging, first, cnt), "export"));
+    SUN_CUDA(cudaMemcpyAsync(host + first * per, L->staging, size_t(cnt * per) * sizeof(double),
+                             cudaMemcpyDeviceToHost, L->stream));
+  }
+  SUN_CUDA(cudaStreamSynchronize(L->stream));
+  return SUN_OK;
+}
+
+sun_status sun_import_links(sun_lattice* L, const double* host, size_t n) {
+  if (!L || !host) return fail(SUN_ERR_ARG, "NULL argument");
+  if (n != canonical_doubles(L)) return fail(SUN_ERR_ARG, "host buffer holds %zu doubles, need %zu", n, canonical_doubles(L));
+  SUN_TRY(set_device(L));
+  const sun::Ctx c = ctx_on(L, L->stream);
+  const int64_t total = 4 * L->ctx.g.V, per = 2 * L->nc * L->nc;
+  for (int64_t first = 0; first < total; first += L->plan.staging_links) {
+    const int64_t cnt = (total - first) < L->plan.staging_links ? (total - first) : L->plan.staging_links;
+    SUN_CUDA(cudaMemcpyAsync(L->staging, host + first * per, size_t(cnt * per) * sizeof(double),
+                             cudaMemcpyHostToDevice, L->stream));
+    SUN_TRY(check_launch(L->ops->import_links(c, L->staging, first, cnt), "import"));
+  }
+  SUN_CUDA(cudaStreamSynchronize(L->stream));
+  return SUN_OK;
+}
+
+sun_status sun_get_heatbath_step(sun_lattice* L, uint64_t* step) {
+  if (!L || !step) return fail(SUN_ERR_ARG, "NULL argument");
+  SUN_TRY(set_device(L));
+  uint32_t v = 0;
+  SUN_CUDA(cudaMemcpyAsync(L->host_results, &L->ctx.state->hb_step, sizeof(uint32_t), cudaMemcpyDeviceToHost, L->stream));
+  SUN_CUDA(cudaStreamSynchronize(L->stream));
+  std::memcpy(&v, L->host_results, sizeof(v));
+  *step = v;
+  return SUN_OK;
+}
+
+sun_status sun_set_heatbath_step(sun_lattice* L, uint64_t step) {
+  if (!L) return fail(SUN_ERR_ARG, "lattice is NULL");
+  if (step > 0xffffffffull) return fail(SUN_ERR_ARG, "heatbath step counter is 32-bit");
+  SUN_TRY(set_device(L));
+  const uint32_t v = uint32_t(step);
+  SUN_CUDA(cudaStreamSynchronize(L->stream));
+  std::memcpy(L->host_results, &v, sizeof(v));
+  SUN_CUDA(cudaMemcpyAsync(&L->ctx.state->hb_step, L->host_results, sizeof(uint32_t), cudaMemcpyHostToDevice, L->stream));
+  SUN_CUDA(cudaStreamSynchronize(L->stream));
+  return SUN_OK;
+}
+
+sun_status sun_set_beta(sun_lattice* L, double beta) {
+  if (!L) return fail(SUN_ERR_ARG, "lattice is NULL");
+  if (!(beta >= 0.0)) return fail(SUN_ERR_ARG, "beta must be >= 0");
+  if (beta != L->beta) {
+    SUN_TRY(set_device(L));
+    SUN_CUDA(cudaStreamSynchronize(L->stream));
+    drop_graphs(L);
+    L->beta = beta;
+  }
+  return SUN_OK;
+}
+
+sun_status sun_synchronize(sun_lattice* L) {
+  if (!L) return fail(SUN_ERR_ARG, "lattice is NULL");
+  SUN_TRY(set_device(L));
+  SUN_CUDA(cudaStreamSynchronize(L->stream));
+  return SUN_OK;
+}
+
+sun_status sun_get_info(const sun_lattice* L, sun_lattice_info* info) {
+  if (!L || !info) return fail(SUN_ERR_ARG, "NULL argument");
+  std::memset(info, 0, sizeof(*info));
+  info->nc = L->nc;
+  info->precision = L->precision;
+  info->storage = L->storage;
+  for (int m = 0; m < 4; ++m) info->dims[m] = L->dims[m];
+  info->beta = L->beta;
+  info->seed = L->seed;
+  info->link_bytes = size_t(L->ops->link_bytes);
+  info->links_bytes = L->plan.links_bytes;
+  info->footprint = L->plan.total;
+  info->links = L->ctx.links;
+  info->stream = L->stream;
+  return SUN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,704 @@
+// sun_kernels.cuh -- kernel templates of the SU(Nc) chessboard link sweep and the
+// per-(Nc, storage, precision) operation table built from them.
+//
+// Included by exactly one translation unit per Nc (ops_su*.cu), which
+// instantiates the table entries it needs.
+#pragma once
+
+#include "sun_device.cuh"
+
+namespace sun {
+
+constexpr int kMaxBlockThreads = 256;
+constexpr int kHeatbathMode = 0;
+constexpr int kOverrelaxMode = 1;
+
+__device__ __forceinline__ int64_t stride_of(const Geom& g, int d) {
+  return d == 0 ? g.stride[0] : (d == 1 ? g.stride[1] : (d == 2 ? g.stride[2] : g.stride[3]));
+}
+__device__ __forceinline__ int64_t fwd(const Geom& g, int64_t lex, int coord, int d) {
+  const int n = dim_of(g, d);
+  const int64_t st = stride_of(g, d);
+  return coord == n - 1 ? lex - int64_t(n - 1) * st : lex + st;
+}
+__device__ __forceinline__ int64_t bwd(const Geom& g, int64_t lex, int coord, int d) {
+  const int n = dim_of(g, d);
+  const int64_t st = stride_of(g, d);
+  return coord == 0 ? lex + int64_t(n - 1) * st : lex - st;
+}
+
+struct PassParams {
+  char* links;
+  int64_t block_bytes;  // bytes of one (direction, parity) block
+  Geom g;
+  int mu, parity;
+  double alpha_coef;  // 2 beta / Nc: heatbath strength alpha = alpha_coef * k
+  uint2 key;
+  const uint32_t* hb_step;
+  uint32_t step_offset;
+};
+
+__device__ __forceinline__ const char* block_ptr(const PassParams& p, int d, int par) {
+  return p.links + (2 * d + par) * p.block_bytes;
+}
+
+// Left-multiply rows i, j of m by the SU(2) element a embedded in the (i,j) subgroup.
+template <class R, int N>
+__device__ __forceinline__ void apply_rows(Mat<R, N>& m, int i, int j, const Quat<R>& a) {
+  const Cpx<R> A00 = {a.a0, a.a3}, A01 = {a.a2, a.a1}, A10 = {-a.a2, a.a1}, A11 = {a.a0, -a.a3};
+#pragma unroll
+  for (int c = 0; c < N; ++c) {
+    const Cpx<R> ri = m.e[i][c], rj = m.e[j][c];
+    Cpx<R> ni = cmul(A00, ri), nj = cmul(A10, ri);
+    cfma(ni, A01, rj);
+    cfma(nj, A11, rj);
+    m.e[i][c] = ni;
+    m.e[j][c] = nj;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One chessboard pass over matrices (Nc >= 2, full or two-row storage):
+// staple (Eq. 9) -> W = U Sigma^+ -> SU(2) subgroups in lexicographic order
+// (Eq. 15), heatbath (Eqs. 12-14) or overrelaxation (Eq. 17) -> store.
+// One thread per link of the pass.
+// ---------------------------------------------------------------------------
+template <class R, int N, int S, int MODE>
+__global__ void __launch_bounds__(kMaxBlockThreads) update_pass_mat(const PassParams p) {
+  const int64_t h = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const Geom& g = p.g;
+  if (h >= g.Vh) return;
+  const int mu = p.mu, par = p.parity, opp = par ^ 1;
+  const Site s = decode_half(g, h, par);
+  const int cmu = coord_of(s, mu);
+  const int64_t lex_pmu = fwd(g, s.lex, cmu, mu);
+
+  Mat<R, N> st;
+  mat_zero(st);
+#pragma unroll
+  for (int nu = 0; nu < 4; ++nu) {
+    if (nu == mu) continue;
+    const int cnu = s.c[nu];
+    const int64_t lex_pnu = fwd(g, s.lex, cnu, nu);
+    const int64_t lex_mnu = bwd(g, s.lex, cnu, nu);
+    const int64_t lex_mnu_pmu = fwd(g, lex_mnu, cmu, mu);
+    {  // U_nu(x) U_mu(x+nu) U_nu(x+mu)^+
+      const Mat<R, N> a = load_mat<R, N, S>(block_ptr(p, nu, par), g.Vh, h);
+      const Mat<R, N> b = load_mat<R, N, S>(block_ptr(p, mu, opp), g.Vh, lex_pnu >> 1);
+      const Mat<R, N> t = mul_nn(a, b);
+      const Mat<R, N> c = load_mat<R, N, S>(block_ptr(p, nu, opp), g.Vh, lex_pmu >> 1);
+      acc_nd(st, t, c);
+    }
+    {  // U_nu(x-nu)^+ U_mu(x-nu) U_nu(x-nu+mu)
+      const Mat<R, N> a = load_mat<R, N, S>(block_ptr(p, nu, opp), g.Vh, lex_mnu >> 1);
+      const Mat<R, N> b = load_mat<R, N, S>(block_ptr(p, mu, opp), g.Vh, lex_mnu >> 1);
+      const Mat<R, N> t = mul_dn(a, b);
+      const Mat<R, N> c = load_mat<R, N, S>(block_ptr(p, nu, par), g.Vh, lex_mnu_pmu >> 1);
+      acc_nn(st, t, c);
+    }
+  }
+
+  char* ublk = p.links + (2 * mu + par) * p.block_bytes;
+  Mat<R, N> u = load_mat<R, N, S, false>(ublk, g.Vh, h);
+  Mat<R, N> w = mul_nd(u, st);
+
+  uint32_t step = 0;
+  if constexpr (MODE == kHeatbathMode) step = *p.hb_step + p.step_offset;
+  const uint32_t link_id = uint32_t(mu) * uint32_t(g.V) + uint32_t(s.lex);
+  const R alpha_coef = R(p.alpha_coef);
+
+  int sub = 0;
+#pragma unroll
+  for (int i = 0; i < N - 1; ++i) {
+#pragma unroll
+    for (int j = i + 1; j < N; ++j) {
+      const bool last = (i == N - 2) && (j == N - 1);
+      const Quat<R> v = block_to_quat(w.e[i][i], w.e[i][j], w.e[j][i], w.e[j][j]);
+      const R k = d_sqrt(v.a0 * v.a0 + v.a1 * v.a1 + v.a2 * v.a2 + v.a3 * v.a3);
+      if (k > R(1e-15) && d_isfinite(k)) {
+        const R inv = R(1) / k;
+        const Quat<R> vd = {v.a0 * inv, -v.a1 * inv, -v.a2 * inv, -v.a3 * inv};  // vhat^+
+        Quat<R> a;
+        bool apply = true;
+        if constexpr (MODE == kHeatbathMode) {
+          Quat<R> b;
+          apply = heatbath_su2<R>(alpha_coef * k, p.key, link_id, step, uint32_t(sub), b);
+          a = qmul(b, vd);
+        } else {
+          a = qmul(vd, vd);
+        }
+        if (apply) {
+          apply_rows(u, i, j, a);
+          if (!last) apply_rows(w, i, j, a);
+        }
+      }
+      ++sub;
+    }
+  }
+  store_mat<R, N, S>(ublk, g.Vh, h, u);
+}
+
+// ---------------------------------------------------------------------------
+// One chessboard pass for SU(2) stored as quaternions (Eq. 6): the same steps
+// with the staple kept in the real span of SU(2).
+// ---------------------------------------------------------------------------
+template <class R, int MODE>
+__global__ void __launch_bounds__(kMaxBlockThreads) update_pass_quat(const PassParams p) {
+  const int64_t h = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const Geom& g = p.g;
+  if (h >= g.Vh) return;
+  const int mu = p.mu, par = p.parity, opp = par ^ 1;
+  const Site s = decode_half(g, h, par);
+  const int cmu = coord_of(s, mu);
+  const int64_t lex_pmu = fwd(g, s.lex, cmu, mu);
+
+  Quat<R> st = {R(0), R(0), R(0), R(0)};
+#pragma unroll
+  for (int nu = 0; nu < 4; ++nu) {
+    if (nu == mu) continue;
+    const int cnu = s.c[nu];
+    const int64_t lex_pnu = fwd(g, s.lex, cnu, nu);
+    const int64_t lex_mnu = bwd(g, s.lex, cnu, nu);
+    const int64_t lex_mnu_pmu = fwd(g, lex_mnu, cmu, mu);
+    {
+      const Quat<R> a = load_quat<R>(block_ptr(p, nu, par), g.Vh, h);
+      const Quat<R> b = load_quat<R>(block_ptr(p, mu, opp), g.Vh, lex_pnu >> 1);
+      const Quat<R> c = load_quat<R>(block_ptr(p, nu, opp), g.Vh, lex_pmu >> 1);
+      st = qadd(st, qmul(qmul(a, b), qdag(c)));
+    }
+    {
+      const Quat<R> a = load_quat<R>(block_ptr(p, nu, opp), g.Vh, lex_mnu >> 1);
+      const Quat<R> b = load_quat<R>(block_ptr(p, mu, opp), g.Vh, lex_mnu >> 1);
+      const Quat<R> c = load_quat<R>(block_ptr(p, nu, par), g.Vh, lex_mnu_pmu >> 1);
+      st = qadd(st, qmul(qmul(qdag(a), b), c));
+    }
+  }
+  char* ublk = p.links + (2 * mu + par) * p.block_bytes;
+  Quat<R> u = load_quat<R, false>(ublk, g.Vh, h);
+  const Quat<R> w = qmul(u, qdag(st));
+  const R k = d_sqrt(w.a0 * w.a0 + w.a1 * w.a1 + w.a2 * w.a2 + w.a3 * w.a3);
+  if (k > R(1e-15) && d_isfinite(k)) {
+    const R inv = R(1) / k;
+    const Quat<R> vd = {w.a0 * inv, -w.a1 * inv, -w.a2 * inv, -w.a3 * inv};
+    if constexpr (MODE == kHeatbathMode) {
+      const uint32_t step = *p.hb_step + p.step_offset;
+      const uint32_t link_id = uint32_t(mu) * uint32_t(g.V) + uint32_t(s.lex);
+      Quat<R> b;
+      if (heatbath_su2<R>(R(p.alpha_coef) * k, p.key, link_id, step, 0u, b)) u = qmul(qmul(b, vd), u);
+    } else {
+      u = qmul(qmul(vd, vd), u);
+    }
+  }
+  store_quat<R>(ublk, g.Vh, h, u);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 re-unitarization of one matrix (Sec. 2).
+// ---------------------------------------------------------------------------
+template <int N>
+__device__ __forceinline__ void normalise_row(Mat<double, N>& m, int r) {
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < N; ++c) s += m.e[r][c].re * m.e[r][c].re + m.e[r][c].im * m.e[r][c].im;
+  const double inv = 1.0 / sqrt(s);
+#pragma unroll
+  for (int c = 0; c < N; ++c) {
+    m.e[r][c].re *= inv;
+    m.e[r][c].im *= inv;
+  }
+}
+
+template <int N>
+__device__ __forceinline__ Cpx<double> det_lu(Mat<double, N> a) {
+  Cpx<double> det = {1.0, 0.0};
+#pragma unroll
+  for (int c = 0; c < N; ++c) {
+    // partial pivoting on |a_rc|
+    int piv = c;
+    double best = a.e[c][c].re * a.e[c][c].re + a.e[c][c].im * a.e[c][c].im;
+#pragma unroll
+    for (int r = c + 1; r < N; ++r) {
+      const double m2 = a.e[r][c].re * a.e[r][c].re + a.e[r][c].im * a.e[r][c].im;
+      if (m2 > best) {
+        best = m2;
+        piv = r;
+      }
+    }
+    if (best == 0.0) return {0.0, 0.0};
+    if (piv != c) {
+#pragma unroll
+      for (int r = c + 1; r < N; ++r) {
+        if (r == piv) {
+#pragma unroll
+          for (int k = 0; k < N; ++k) {
+            const Cpx<double> t = a.e[c][k];
+            a.e[c][k] = a.e[r][k];
+            a.e[r][k] = t;
+          }
+        }
+      }
+      det = {-det.re, -det.im};
+    }
+    const Cpx<double> d = a.e[c][c];
+    det = cmul(det, d);
+    const double inv2 = 1.0 / best;
+    const Cpx<double> dinv = {d.re * inv2, -d.im * inv2};
+#pragma unroll
+    for (int r = c + 1; r < N; ++r) {
+      const Cpx<double> f = cmul(a.e[r][c], dinv);
+#pragma unroll
+      for (int k = c; k < N; ++k) {
+        const Cpx<double> t = cmul(f, a.e[c][k]);
+        a.e[r][k].re -= t.re;
+        a.e[r][k].im -= t.im;
+      }
+    }
+  }
+  return det;
+}
+
+template <int N>
+__device__ __forceinline__ void reunit_d(Mat<double, N>& m) {
+  if constexpr (N == 2) {
+    normalise_row<2>(m, 0);
+    m.e[1][0] = {-m.e[0][1].re, m.e[0][1].im};
+    m.e[1][1] = {m.e[0][0].re, -m.e[0][0].im};
+  } else {
+    constexpr int rows = (N == 3) ? 2 : N;
+#pragma unroll
+    for (int r = 0; r < rows; ++r) {
+#pragma unroll
+      for (int q = 0; q < r; ++q) {
+        Cpx<double> pr = {0.0, 0.0};
+#pragma unroll
+        for (int c = 0; c < N; ++c) ccfma(pr, m.e[q][c], m.e[r][c]);
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+          const Cpx<double> t = cmul(pr, m.e[q][c]);
+          m.e[r][c].re -= t.re;
+          m.e[r][c].im -= t.im;
+        }
+      }
+      normalise_row<N>(m, r);
+    }
+    if constexpr (N == 3) {
+      su3_third_row(m);
+    } else {
+      const Cpx<double> d = det_lu<N>(m);
+      const double inv = 1.0 / sqrt(d.re * d.re + d.im * d.im);
+      const Cpx<double> ph = {d.re * inv, -d.im * inv};
+#pragma unroll
+      for (int c = 0; c < N; ++c) m.e[N - 1][c] = cmul(m.e[N - 1][c], ph);
+    }
+  }
+}
+
+template <class A, class B, int N>
+__device__ __forceinline__ Mat<B, N> mat_cast(const Mat<A, N>& m) {
+  Mat<B, N> o;
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = 0; j < N; ++j) o.e[i][j] = {B(m.e[i][j].re), B(m.e[i][j].im)};
+  return o;
+}
+
+struct LinkParams {
+  char* links;
+  int64_t block_bytes;
+  Geom g;
+  uint2 key;
+  int hot;
+};
+
+template <class R, int N, int S>
+__global__ void __launch_bounds__(256) reunit_kernel(const LinkParams p) {
+  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= 8 * p.g.Vh) return;
+  const int b = int(idx / p.g.Vh);
+  const int64_t h = idx - int64_t(b) * p.g.Vh;
+  char* blk = p.links + b * p.block_bytes;
+  if constexpr (S == kQuat) {
+    const Quat<R> q = load_quat<R, false>(blk, p.g.Vh, h);
+    const double a0 = q.a0, a1 = q.a1, a2 = q.a2, a3 = q.a3;
+    const double inv = 1.0 / sqrt(a0 * a0 + a3 * a3 + a2 * a2 + a1 * a1);
+    store_quat<R>(blk, p.g.Vh, h, Quat<R>{R(a0 * inv), R(a1 * inv), R(a2 * inv), R(a3 * inv)});
+  } else {
+    Mat<double, N> m = mat_cast<R, double, N>(load_mat<R, N, S, false>(blk, p.g.Vh, h));
+    reunit_d<N>(m);
+    store_mat<R, N, S>(blk, p.g.Vh, h, mat_cast<double, R, N>(m));
+  }
+}
+
+// Cold start: identity.  Hot start: complex Gaussians (Box-Muller on Philox
+// counter (mu*V + lex, 0, call, 2)), row by row, then FP64 re-unitarization
+// (Gram-Schmidt + determinant phase): a Haar-random SU(Nc) matrix.
+template <class R, int N, int S>
+__global__ void __launch_bounds__(256) init_kernel(const LinkParams p) {
+  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= 8 * p.g.Vh) return;
+  const int b = int(idx / p.g.Vh);
+  const int64_t h = idx - int64_t(b) * p.g.Vh;
+  const int mu = b >> 1, par = b & 1;
+  char* blk = p.links + b * p.block_bytes;
+  Mat<double, N> m;
+  if (!p.hot) {
+    mat_identity(m);
+  } else {
+    const Site s = decode_half(p.g, h, par);
+    const uint32_t link_id = uint32_t(mu) * uint32_t(p.g.V) + uint32_t(s.lex);
+    constexpr int kNormals = 2 * N * N;
+    double gauss[kNormals + 3];
+#pragma unroll
+    for (int call = 0; 4 * call < kNormals; ++call) {
+      const uint4 u = philox4x32_10(make_uint4(link_id, 0u, uint32_t(call), kTagInit), p.key);
+      const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+      for (int pair = 0; pair < 2; ++pair) {
+        const double rad = sqrt(-2.0 * log(u01<double>(w[2 * pair])));
+        double sn, cs;
+        sincospi(2.0 * u01<double>(w[2 * pair + 1]), &sn, &cs);
+        if (4 * call + 2 * pair < kNormals) gauss[4 * call + 2 * pair] = rad * cs;
+        if (4 * call + 2 * pair + 1 < kNormals) gauss[4 * call + 2 * pair + 1] = rad * sn;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+#pragma unroll
+      for (int j = 0; j < N; ++j) m.e[i][j] = {gauss[2 * (N * i + j)], gauss[2 * (N * i + j) + 1]};
+    reunit_d<N>(m);
+  }
+  store_mat<R, N, S>(blk, p.g.Vh, h, mat_cast<double, R, N>(m));
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic FP64 reductions: per-thread sums -> warp shuffles -> block ->
+// one partial per block; the last block to finish adds the partials in block
+// order and writes the scaled result, then re-arms the counter.
+// ---------------------------------------------------------------------------
+struct ReduceParams {
+  double* partials;      // [gridDim.x * K]
+  unsigned* counter;     // zero before the launch, zero after
+  double* out;           // result slot base
+  const uint32_t* slot;  // optional: results go to out[(*slot % cap) * K + k]
+  int cap;
+  double scale;
+};
+
+template <int K>
+__device__ __forceinline__ void reduce_finish(double (&v)[K], const ReduceParams& rp) {
+  __shared__ double sh[kMaxBlockThreads / 32][K];
+  __shared__ bool am_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    if (lane == 0) sh[warp][k] = v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double s = 0.0;
+      for (int w = 0; w < nwarps; ++w) s += sh[w][k];
+      rp.partials[blockIdx.x * K + k] = s;
+    }
+    __threadfence();
+    const unsigned done = atomicAdd(rp.counter, 1u);
+    am_last = (done == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double s = 0.0;
+      for (int b = lane; b < int(gridDim.x); b += 32) s += __ldcg(&rp.partials[b * K + k]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      if (lane == 0) {
+        const int idx = rp.slot ? int(*rp.slot % uint32_t(rp.cap)) : 0;
+        rp.out[idx * K + k] = s * rp.scale;
+      }
+    }
+    if (lane == 0) *rp.counter = 0u;
+  }
+}
+
+struct ObsParams {
+  const char* links;
+  int64_t block_bytes;
+  Geom g;
+};
+
+__device__ __forceinline__ const char* obs_block(const ObsParams& p, int d, int par) {
+  return p.links + (2 * d + par) * p.block_bytes;
+}
+
+// <P>: every site, the six plaquettes P_{mu nu}(x) = U_mu(x) U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+
+// (Eq. 4), ReTr in the storage precision, accumulated in FP64.
+template <class R, int N, int S>
+__global__ void __launch_bounds__(256) plaquette_kernel(const ObsParams p, const ReduceParams rp) {
+  const Geom& g = p.g;
+  double acc[1] = {0.0};
+  for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < g.V;
+       idx += int64_t(gridDim.x) * blockDim.x) {
+    const int par = idx >= g.Vh ? 1 : 0;
+    const int64_t h = idx - par * g.Vh;
+    const Site s = decode_half(g, h, par);
+#pragma unroll
+    for (int mu = 0; mu < 3; ++mu) {
+      const int64_t xpmu = fwd(g, s.lex, s.c[mu], mu) >> 1;
+#pragma unroll
+      for (int nu = mu + 1; nu < 4; ++nu) {
+        const int64_t xpnu = fwd(g, s.lex, s.c[nu], nu) >> 1;
+        if constexpr (S == kQuat) {
+          const Quat<R> umx = load_quat<R>(obs_block(p, mu, par), g.Vh, h);
+          const Quat<R> unx = load_quat<R>(obs_block(p, nu, par), g.Vh, h);
+          const Quat<R> t1 = qmul(umx, load_quat<R>(obs_block(p, nu, par ^ 1), g.Vh, xpmu));
+          const Quat<R> t2 = qmul(unx, load_quat<R>(obs_block(p, mu, par ^ 1), g.Vh, xpnu));
+          acc[0] += double(R(2) * (t1.a0 * t2.a0 + t1.a1 * t2.a1 + t1.a2 * t2.a2 + t1.a3 * t2.a3));
+        } else {
+          const Mat<R, N> t1 = mul_nn(load_mat<R, N, S>(obs_block(p, mu, par), g.Vh, h),
+                                      load_mat<R, N, S>(obs_block(p, nu, par ^ 1), g.Vh, xpmu));
+          const Mat<R, N> t2 = mul_nn(load_mat<R, N, S>(obs_block(p, nu, par), g.Vh, h),
+                                      load_mat<R, N, S>(obs_block(p, mu, par ^ 1), g.Vh, xpnu));
+          acc[0] += double(retr_nd(t1, t2));
+        }
+      }
+    }
+  }
+  reduce_finish<1>(acc, rp);
+}
+
+// Polyakov loop: every spatial site, Tr of the ordered product of U_t over t,
+// products in the storage precision, accumulated in FP64 (re, im).
+template <class R, int N, int S>
+__global__ void __launch_bounds__(256) polyakov_kernel(const ObsParams p, const ReduceParams rp) {
+  const Geom& g = p.g;
+  const int64_t nsp = int64_t(g.nx) * g.ny * g.nz;
+  double acc[2] = {0.0, 0.0};
+  for (int64_t xs = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; xs < nsp;
+       xs += int64_t(gridDim.x) * blockDim.x) {
+    const int x = int(xs % g.nx);
+    const int y = int((xs / g.nx) % g.ny);
+    const int z = int(xs / (int64_t(g.nx) * g.ny));
+    const int sp = (x + y + z) & 1;
+    if constexpr (S == kQuat) {
+      Quat<R> P = load_quat<R>(obs_block(p, 3, sp), g.Vh, xs >> 1);
+      for (int t = 1; t < g.nt; ++t) {
+        const int64_t lex = xs + int64_t(t) * nsp;
+        P = qmul(P, load_quat<R>(obs_block(p, 3, (sp + t) & 1), g.Vh, lex >> 1));
+      }
+      acc[0] += double(R(2) * P.a0);  // Tr of [[a0 + i a3, .], [., a0 - i a3]] is real
+    } else {
+      Mat<R, N> P = load_mat<R, N, S>(obs_block(p, 3, sp), g.Vh, xs >> 1);
+      for (int t = 1; t < g.nt; ++t) {
+        const int64_t lex = xs + int64_t(t) * nsp;
+        P = mul_nn(P, load_mat<R, N, S>(obs_block(p, 3, (sp + t) & 1), g.Vh, lex >> 1));
+      }
+#pragma unroll
+      for (int d = 0; d < N; ++d) {
+        acc[0] += double(P.e[d][d].re);
+        acc[1] += double(P.e[d][d].im);
+      }
+    }
+  }
+  reduce_finish<2>(acc, rp);
+}
+
+// ---------------------------------------------------------------------------
+// Canonical FP64 <-> storage conversion of links [first, first + count),
+// canonical link index l = mu * V + lex.
+// ---------------------------------------------------------------------------
+template <class R, int N, int S>
+__global__ void __launch_bounds__(256) export_kernel(const ObsParams p, double* dst, int64_t first, int64_t count) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const int64_t l = first + i;
+  const int mu = int(l / p.g.V);
+  const int64_t lex = l - int64_t(mu) * p.g.V;
+  const int x = int(lex % p.g.nx), y = int((lex / p.g.nx) % p.g.ny);
+  const int z = int((lex / (int64_t(p.g.nx) * p.g.ny)) % p.g.nz), t = int(lex / (int64_t(p.g.nx) * p.g.ny * p.g.nz));
+  const int par = (x + y + z + t) & 1;
+  const Mat<R, N> m = load_mat<R, N, S>(obs_block(p, mu, par), p.g.Vh, lex >> 1);
+  double* o = dst + i * (2 * N * N);
+  if constexpr (S == kTwoRow) {
+    // rebuild the third row in FP64 from the stored rows
+    Mat<double, 3> d = mat_cast<R, double, 3>(m);
+    su3_third_row(d);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        o[2 * (3 * a + b)] = d.e[a][b].re;
+        o[2 * (3 * a + b) + 1] = d.e[a][b].im;
+      }
+  } else {
+#pragma unroll
+    for (int a = 0; a < N; ++a)
+#pragma unroll
+      for (int b = 0; b < N; ++b) {
+        o[2 * (N * a + b)] = double(m.e[a][b].re);
+        o[2 * (N * a + b) + 1] = double(m.e[a][b].im);
+      }
+  }
+}
+
+template <class R, int N, int S>
+__global__ void __launch_bounds__(256) import_kernel(const ObsParams p, const double* src, int64_t first, int64_t count) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const int64_t l = first + i;
+  const int mu = int(l / p.g.V);
+  const int64_t lex = l - int64_t(mu) * p.g.V;
+  const int x = int(lex % p.g.nx), y = int((lex / p.g.nx) % p.g.ny);
+  const int z = int((lex / (int64_t(p.g.nx) * p.g.ny)) % p.g.nz), t = int(lex / (int64_t(p.g.nx) * p.g.ny * p.g.nz));
+  const int par = (x + y + z + t) & 1;
+  const double* s = src + i * (2 * N * N);
+  Mat<R, N> m;
+#pragma unroll
+  for (int a = 0; a < N; ++a)
+#pragma unroll
+    for (int b = 0; b < N; ++b) m.e[a][b] = {R(s[2 * (N * a + b)]), R(s[2 * (N * a + b) + 1])};
+  store_mat<R, N, S>(const_cast<char*>(obs_block(p, mu, par)), p.g.Vh, lex >> 1, m);
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers and the operation table
+// ---------------------------------------------------------------------------
+inline PassParams make_pass_params(const Ctx& c, int mu, int parity, uint32_t step_offset) {
+  PassParams p;
+  p.links = c.links;
+  p.block_bytes = c.block_bytes;
+  p.g = c.g;
+  p.mu = mu;
+  p.parity = parity;
+  p.alpha_coef = 2.0 * c.beta / c.nc;
+  p.key = make_uint2(uint32_t(c.seed & 0xffffffffu), uint32_t(c.seed >> 32));
+  p.hb_step = &c.state->hb_step;
+  p.step_offset = step_offset;
+  return p;
+}
+
+template <class R, int N, int S>
+cudaError_t launch_pass(const Ctx& c, int mode, int mu, int parity, uint32_t step_offset) {
+  const PassParams p = make_pass_params(c, mu, parity, step_offset);
+  const int bt = c.block_threads;
+  const unsigned grid = unsigned((c.g.Vh + bt - 1) / bt);
+  if constexpr (S == kQuat) {
+    if (mode == kHeatbathMode)
+      update_pass_quat<R, kHeatbathMode><<<grid, bt, 0, c.stream>>>(p);
+    else
+      update_pass_quat<R, kOverrelaxMode><<<grid, bt, 0, c.stream>>>(p);
+  } else {
+    if (mode == kHeatbathMode)
+      update_pass_mat<R, N, S, kHeatbathMode><<<grid, bt, 0, c.stream>>>(p);
+    else
+      update_pass_mat<R, N, S, kOverrelaxMode><<<grid, bt, 0, c.stream>>>(p);
+  }
+  return cudaGetLastError();
+}
+
+inline LinkParams make_link_params(const Ctx& c, int hot) {
+  LinkParams p;
+  p.links = c.links;
+  p.block_bytes = c.block_bytes;
+  p.g = c.g;
+  p.key = make_uint2(uint32_t(c.seed & 0xffffffffu), uint32_t(c.seed >> 32));
+  p.hot = hot;
+  return p;
+}
+
+template <class R, int N, int S>
+cudaError_t launch_init(const Ctx& c, int hot) {
+  const int64_t n = 8 * c.g.Vh;
+  init_kernel<R, N, S><<<unsigned((n + 127) / 128), 128, 0, c.stream>>>(make_link_params(c, hot));
+  return cudaGetLastError();
+}
+
+template <class R, int N, int S>
+cudaError_t launch_reunit(const Ctx& c) {
+  const int64_t n = 8 * c.g.Vh;
+  reunit_kernel<R, N, S><<<unsigned((n + 127) / 128), 128, 0, c.stream>>>(make_link_params(c, 0));
+  return cudaGetLastError();
+}
+
+inline ObsParams make_obs_params(const Ctx& c) {
+  ObsParams p;
+  p.links = c.links;
+  p.block_bytes = c.block_bytes;
+  p.g = c.g;
+  return p;
+}
+
+inline unsigned reduce_grid(const Ctx& c, int64_t items, int bt) {
+  int64_t want = (items + bt - 1) / bt;
+  int64_t cap = int64_t(c.reduce_blocks);
+  return unsigned(want < cap ? (want < 1 ? 1 : want) : cap);
+}
+
+template <class R, int N, int S>
+cudaError_t launch_plaquette(const Ctx& c, double* out, const uint32_t* slot, int cap) {
+  ReduceParams rp;
+  rp.partials = c.partials;
+  rp.counter = &c.state->plaq_counter;
+  rp.out = out;
+  rp.slot = slot;
+  rp.cap = cap;
+  rp.scale = 1.0 / (6.0 * double(c.g.V) * N);
+  const int bt = 256;
+  plaquette_kernel<R, N, S><<<reduce_grid(c, c.g.V, bt), bt, 0, c.stream>>>(make_obs_params(c), rp);
+  return cudaGetLastError();
+}
+
+template <class R, int N, int S>
+cudaError_t launch_polyakov(const Ctx& c, double* out, const uint32_t* slot, int cap) {
+  ReduceParams rp;
+  rp.partials = c.partials + 2 * kMaxReduceBlocks;
+  rp.counter = &c.state->poly_counter;
+  rp.out = out;
+  rp.slot = slot;
+  rp.cap = cap;
+  const int64_t nsp = int64_t(c.g.nx) * c.g.ny * c.g.nz;
+  rp.scale = 1.0 / (double(N) * double(nsp));
+  const int bt = 128;
+  polyakov_kernel<R, N, S><<<reduce_grid(c, nsp, bt), bt, 0, c.stream>>>(make_obs_params(c), rp);
+  return cudaGetLastError();
+}
+
+template <class R, int N, int S>
+cudaError_t launch_export(const Ctx& c, double* dst, int64_t first, int64_t count) {
+  if (count <= 0) return cudaSuccess;
+  export_kernel<R, N, S><<<unsigned((count + 127) / 128), 128, 0, c.stream>>>(make_obs_params(c), dst, first, count);
+  return cudaGetLastError();
+}
+
+template <class R, int N, int S>
+cudaError_t launch_import(const Ctx& c, const double* src, int64_t first, int64_t count) {
+  if (count <= 0) return cudaSuccess;
+  import_kernel<R, N, S><<<unsigned((count + 127) / 128), 128, 0, c.stream>>>(make_obs_params(c), src, first, count);
+  return cudaGetLastError();
+}
+
+template <class R, int N, int S>
+const Ops* ops_instance() {
+  static const Ops ops = {
+      N,
+      Layout<R, N, S>::nreals,
+      int(sizeof(R)) * 8,
+      Layout<R, N, S>::bytes,
+      &launch_pass<R, N, S>,
+      &launch_init<R, N, S>,
+      &launch_reunit<R, N, S>,
+      &launch_plaquette<R, N, S>,
+      &launch_polyakov<R, N, S>,
+      &launch_export<R, N, S>,
+      &launch_import<R, N, S>,
+  };
+  return &ops;
+}
+
+}  // namespace sun

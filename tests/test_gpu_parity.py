@@ -1,0 +1,402 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle on
+the same seeded inputs and the same Philox stream.
+
+Tolerances: FP64 storage 1e-12 per pass, FP32 storage 1e-5 per pass (the
+bounds stated for overrelaxation links).  Heatbath links are compared where
+the accept/reject branch agrees; a link whose draw took a different branch
+(an "FP flip") differs by O(1) and is counted, at most 1e-6 of the updates.
+"""
+import numpy as np
+import pytest
+
+import oracle as orc
+from tests.inputs import near_identity_config, random_gauge_config
+
+pytestmark = pytest.mark.gpu
+
+# (nc, storage, precision): every built combination
+CONFIGS = [(2, 4, 64), (2, 4, 32), (2, 8, 64), (2, 8, 32), (3, 12, 32), (3, 18, 32), (3, 12, 64), (3, 18, 64),
+           (4, 32, 32), (4, 32, 64), (5, 50, 32), (6, 72, 32), (6, 72, 64)]
+
+
+def tol(prec):
+    return 1e-12 if prec == 64 else 1e-5
+
+
+def beta_for(nc):
+    return 2.3 if nc == 2 else (6.0 if nc == 3 else 0.7 * nc * nc)
+
+
+@pytest.fixture(scope="session")
+def sunlib():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1112_4533_gb300 import build as b
+    b.build()
+    import paper_1112_4533_gb300 as p
+    p.load_library()
+    return p
+
+
+def thermal_config(nc, dims, seed):
+    """Oracle configuration a few heatbath sweeps away from a Haar start."""
+    U = random_gauge_config(nc, dims, seed)
+    orc.sweep(U, beta_for(nc), 2, 1, True, seed + 1, 0)
+    return U
+
+
+def gpu_lattice(p, nc, dims, storage, prec, U=None, seed=7, beta=None, **kw):
+    L = p.Lattice(nc, dims, beta_for(nc) if beta is None else beta, seed=seed, precision=prec, storage=storage, **kw)
+    if U is not None:
+        L.import_links(U)
+    return L
+
+
+def maxdiff(a, b):
+    return float(np.abs(a - b).max())
+
+
+# ------------------------------------------------------------- init / state ----
+
+@pytest.mark.parametrize("cfg", CONFIGS)
+def test_cold_start(sunlib, cfg):
+    nc, st, prec = cfg
+    with gpu_lattice(sunlib, nc, (4, 2, 4, 6), st, prec) as L:
+        U = L.export_links()
+        assert np.array_equal(U, orc.init(nc, (4, 2, 4, 6), False, 1))
+        assert L.plaquette() == 1.0
+        assert L.polyakov_loop() == 1.0
+
+
+@pytest.mark.parametrize("cfg", CONFIGS)
+def test_hot_start_matches_oracle(sunlib, cfg):
+    nc, st, prec = cfg
+    dims = (6, 4, 2, 8)
+    L = sunlib.Lattice(nc, dims, 1.0, hot_start=True, seed=99, precision=prec, storage=st)
+    U = L.export_links()
+    L.close()
+    want = orc.init(nc, dims, True, 99)
+    assert maxdiff(U, want) < (1e-13 if prec == 64 else 5e-7)
+
+
+@pytest.mark.parametrize("cfg", CONFIGS)
+def test_import_export_roundtrip(sunlib, cfg):
+    nc, st, prec = cfg
+    dims = (4, 4, 2, 2)
+    U = random_gauge_config(nc, dims, seed=5)
+    with gpu_lattice(sunlib, nc, dims, st, prec, U) as L:
+        back = L.export_links()
+        assert maxdiff(back, U) < (1e-15 if prec == 64 else 5e-7)
+        L.import_links(back)
+        again = L.export_links()
+        if st == 12:
+            assert maxdiff(again, back) < 5e-7
+        else:
+            assert np.array_equal(again, back)
+
+
+# ----------------------------------------------------------- one pass ----
+
+PASS_DIMS = (8, 6, 4, 10)  # V/2 = 960: several 128-thread blocks and a ragged tail
+
+
+@pytest.mark.parametrize("cfg", CONFIGS)
+def test_overrelaxation_pass_matches_oracle(sunlib, cfg):
+    nc, st, prec = cfg
+    U0 = thermal_config(nc, PASS_DIMS, seed=10 + nc)
+    with gpu_lattice(sunlib, nc, PASS_DIMS, st, prec, U0) as L:
+        start = L.export_links()  # the stored (rounded / two-row) representation
+        for mu, par in [(0, 0), (3, 1), (1, 1), (2, 0)]:
+            before = L.export_links()
+            L.update_pass(sunlib.OVERRELAX, mu, par)
+            got = L.export_links()
+            want = before.copy()
+            orc.update_pass(want, beta_for(nc), orc.OVERRELAX, mu, par, 0, 7)
+            assert maxdiff(got, want) < tol(prec), (mu, par)
+            assert maxdiff(got, before) > 1e-3  # it did something
+        assert maxdiff(start, got) > 1e-3
+
+
+@pytest.mark.parametrize("cfg", CONFIGS)
+def test_heatbath_pass_matches_oracle(sunlib, cfg):
+    nc, st, prec = cfg
+    U0 = thermal_config(nc, PASS_DIMS, seed=20 + nc)
+    n_updates = 0
+    flips = 0
+    with gpu_lattice(sunlib, nc, PASS_DIMS, st, prec, U0, seed=31) as L:
+        L.heatbath_step = 5
+        for mu, par in [(1, 0), (2, 1), (0, 1), (3, 0)]:
+            before = L.export_links()
+            L.update_pass(sunlib.HEATBATH, mu, par)
+            got = L.export_links()
+            want = before.copy()
+            capped = orc.update_pass(want, beta_for(nc), orc.HEATBATH, mu, par, 5, 31)
+            assert capped == 0
+            d = np.abs(got - want).reshape(4, -1, nc * nc).max(axis=2)
+            assert d[[m for m in range(4) if m != mu]].max() == 0
+            flips += int((d[mu] > tol(prec)).sum())
+            n_updates += d.shape[1] // 2
+    assert flips <= 1e-6 * n_updates, (flips, n_updates)
+
+
+# ----------------------------------------------------- reunit and observables ----
+
+@pytest.mark.parametrize("cfg", CONFIGS)
+def test_reunitarization_matches_oracle(sunlib, cfg):
+    nc, st, prec = cfg
+    dims = (4, 2, 2, 4)
+    rng = np.random.default_rng(3)
+    U = random_gauge_config(nc, dims, seed=40)
+    U = U + 1e-3 * (rng.normal(size=U.shape) + 1j * rng.normal(size=U.shape))
+    with gpu_lattice(sunlib, nc, dims, st, prec, U) as L:
+        start = L.export_links()
+        L.reunitarize()
+        got = L.export_links()
+    want = start.copy()
+    orc.reunitarize(want)
+    assert maxdiff(got, want) < (1e-13 if prec == 64 else 5e-7)
+    m = got.reshape(-1, nc, nc)
+    assert np.abs(m @ np.conj(np.swapaxes(m, 1, 2)) - np.eye(nc)).max() < (1e-14 if prec == 64 else 1e-6)
+
+
+@pytest.mark.parametrize("cfg", CONFIGS)
+def test_plaquette_and_polyakov_match_oracle(sunlib, cfg):
+    nc, st, prec = cfg
+    dims = (6, 4, 8, 6)
+    U = random_gauge_config(nc, dims, seed=50)
+    with gpu_lattice(sunlib, nc, dims, st, prec, U) as L:
+        start = L.export_links()
+        p = L.plaquette()
+        poly = L.polyakov_loop()
+        p2 = L.plaquette()
+    assert p == p2  # deterministic reduction
+    t = 1e-14 if prec == 64 else 2e-6
+    assert abs(p - orc.plaquette(start)) < t
+    assert abs(poly - orc.polyakov(start)) < (1e-13 if prec == 64 else 2e-5)
+
+
+# -------------------------------------------------------------- sweeps ----
+
+def test_su2_small_workload_history_matches_oracle(sunlib):
+    """SU(2) 8^4, beta 2.3, cold start, 10 sweeps of 1 heatbath + 4
+    overrelaxation, FP64 links, Philox seed 1, plaquette after each sweep.
+
+    Every sweep is compared from the same input (the oracle restarts from the
+    GPU's exported links): links to 1e-11 and the plaquette to 1e-12.  The
+    free-running histories agree to 1e-10 for the first sweeps only: the chain
+    amplifies rounding-order differences by roughly 30x per sweep."""
+    dims = (8, 8, 8, 8)
+    U = orc.init(2, dims, False, 1)
+    free = U.copy()
+    free_hist = []
+    with sunlib.Lattice(2, dims, 2.3, hot_start=False, seed=1, precision=64) as L:
+        for s in range(10):
+            start = L.export_links()
+            plaq, poly = L.run(1, 1, 4)
+            got = L.export_links()
+            want = start.copy()
+            orc.sweep(want, 2.3, 1, 4, True, 1, s)
+            assert maxdiff(got, want) < 1e-11, s
+            assert abs(plaq[0] - orc.plaquette(want)) < 1e-12, s
+            assert abs(poly[0] - orc.polyakov(want)) < 1e-12, s
+            orc.sweep(free, 2.3, 1, 4, True, 1, s)
+            free_hist.append((plaq[0], orc.plaquette(free)))
+        assert L.heatbath_step == 10
+    d = np.array([abs(a - b) for a, b in free_hist])
+    assert d[:4].max() < 1e-10 and d.max() < 1e-3
+
+
+@pytest.mark.parametrize("nc,st", [(2, 4), (3, 18), (4, 32), (6, 72)])
+def test_fp64_sweeps_follow_the_oracle(sunlib, nc, st):
+    """Three FP64 sweeps, each compared from the same input."""
+    dims = (4, 6, 4, 4)
+    beta = beta_for(nc)
+    with sunlib.Lattice(nc, dims, beta, hot_start=True, seed=17, precision=64, storage=st) as L:
+        for s in range(3):
+            start = L.export_links()
+            L.sweep(1, 2)
+            got = L.export_links()
+            want = start.copy()
+            orc.sweep(want, beta, 1, 2, True, 17, s)
+            assert maxdiff(got, want) < 1e-11, s
+
+
+def test_su3_medium_workload_sweep_pass_by_pass(sunlib):
+    """SU(3) 16^4, beta 6.0, Haar start, FP32 12-real: every pass of one sweep
+    (1 heatbath + 4 overrelaxation steps, 40 passes) and the FP64
+    reunitarization, each compared with the oracle from the same input."""
+    dims = (16, 16, 16, 16)
+    n_updates, flips = 0, 0
+    with sunlib.Lattice(3, dims, 6.0, hot_start=True, seed=2, precision=32, storage=12) as L:
+        hot = L.export_links()
+        assert maxdiff(hot, orc.init(3, dims, True, 2)) < 5e-7
+        for mode in [orc.HEATBATH] + [orc.OVERRELAX] * 4:
+            for mu in range(4):
+                for par in range(2):
+                    before = L.export_links()
+                    L.update_pass(mode, mu, par)
+                    got = L.export_links()
+                    want = before.copy()
+                    orc.update_pass(want, 6.0, mode, mu, par, 0, 2)
+                    d = np.abs(got - want).reshape(4, -1, 9).max(axis=2)[mu]
+                    if mode == orc.HEATBATH:
+                        flips += int((d > 1e-5).sum())
+                        n_updates += d.size // 2
+                    else:
+                        assert d.max() < 1e-5, (mu, par, d.max())
+        before = L.export_links()
+        L.reunitarize()
+        got = L.export_links()
+        orc.reunitarize(before)
+        assert maxdiff(got, before) < 5e-7
+        assert abs(L.plaquette() - orc.plaquette(got)) < 1e-6
+    assert flips <= 1e-6 * n_updates + 1, (flips, n_updates)
+
+
+@pytest.mark.parametrize("nc,beta,st,prec", [(2, 2.3, 4, 32), (3, 6.0, 12, 32)])
+def test_equilibrium_plaquette_agrees_with_oracle(sunlib, nc, beta, st, prec):
+    """Independent chains (different seeds) on 8^4: equilibrium <P> agrees within
+    3 sigma of the combined binned error."""
+    dims = (8, 8, 8, 8)
+    therm, meas = 40, 160
+    with sunlib.Lattice(nc, dims, beta, hot_start=True, seed=1001, precision=prec, storage=st) as L:
+        plaq, _ = L.run(therm + meas, 1, 4, polyakov=False)
+    g = plaq[therm:]
+    U = orc.init(nc, dims, True, 2002)
+    h = []
+    for s in range(therm + meas):
+        orc.sweep(U, beta, 1, 4, True, 2002, s)
+        if s >= therm:
+            h.append(orc.plaquette(U))
+    o = np.array(h)
+
+    def mean_err(x):
+        b = x.reshape(16, -1).mean(axis=1)
+        return x.mean(), b.std(ddof=1) / np.sqrt(len(b))
+
+    mg, eg = mean_err(g)
+    mo, eo = mean_err(o)
+    assert abs(mg - mo) < 3 * np.hypot(eg, eo), (mg, eg, mo, eo)
+
+
+# ------------------------------------------------------- equivalences ----
+
+def test_generic_su2_equals_quaternion_su2(sunlib):
+    dims = (4, 4, 4, 6)
+    U = thermal_config(2, dims, seed=60)
+    out = []
+    for st in (4, 8):
+        with gpu_lattice(sunlib, 2, dims, st, 64, U, seed=3) as L:
+            L.sweep(1, 2)
+            out.append(L.export_links())
+    assert maxdiff(out[0], out[1]) < 1e-13
+
+
+def test_two_row_equals_full_su3(sunlib):
+    dims = (4, 4, 4, 6)
+    U = thermal_config(3, dims, seed=61)
+    out = []
+    for st in (12, 18):
+        with gpu_lattice(sunlib, 3, dims, st, 64, U, seed=3) as L:
+            L.sweep(1, 2)
+            out.append(L.export_links())
+    assert maxdiff(out[0], out[1]) < 1e-12
+
+
+def test_graph_replay_equals_direct_launches(sunlib):
+    dims = (8, 4, 4, 8)
+    res = []
+    for graphs in (True, False):
+        with sunlib.Lattice(3, dims, 6.0, hot_start=True, seed=4, use_graphs=graphs) as L:
+            plaq, poly = L.run(5, 1, 4)
+            res.append((plaq, poly, L.export_links()))
+    assert np.array_equal(res[0][0], res[1][0])
+    assert np.array_equal(res[0][1], res[1][1])
+    assert np.array_equal(res[0][2], res[1][2])
+
+
+def test_runs_are_deterministic(sunlib):
+    out = []
+    for _ in range(2):
+        with sunlib.Lattice(4, (4, 4, 4, 4), 11.2, hot_start=True, seed=8) as L:
+            L.run(3, 1, 2)
+            out.append(L.export_links())
+    assert np.array_equal(out[0], out[1])
+
+
+def test_resume_from_exported_state_is_exact(sunlib):
+    """(links, seed, heatbath step) is the whole state: stopping, exporting and
+    resuming in a fresh lattice reproduces the uninterrupted chain bitwise."""
+    dims = (8, 4, 4, 4)
+    with sunlib.Lattice(3, dims, 6.0, hot_start=True, seed=12) as A:
+        A.run(4, 1, 3)
+        ref = A.export_links()
+    with sunlib.Lattice(3, dims, 6.0, hot_start=True, seed=12) as B:
+        B.run(2, 1, 3)
+        saved, step = B.export_links(), B.heatbath_step
+    with sunlib.Lattice(3, dims, 6.0, hot_start=False, seed=12) as C:
+        C.import_links(saved)
+        C.heatbath_step = step
+        # the export holds the stored rows exactly, so the continuation is bitwise
+        C.run(2, 1, 3)
+        got = C.export_links()
+    assert np.array_equal(got, ref)
+
+
+# ------------------------------------------------------------ edge cases ----
+
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (2, 4, 6, 2), (10, 2, 2, 4)])
+def test_smallest_and_ragged_lattices(sunlib, dims):
+    U0 = thermal_config(3, dims, seed=70)
+    with gpu_lattice(sunlib, 3, dims, 18, 64, U0, seed=5) as L:
+        L.sweep(1, 1)
+        got = L.export_links()
+        p = L.plaquette()
+    want = U0.copy()
+    orc.sweep(want, 6.0, 1, 1, True, 5, 0)
+    assert maxdiff(got, want) < 1e-11
+    assert abs(p - orc.plaquette(want)) < 1e-13
+
+
+def test_beta_zero_heatbath_gives_haar_links(sunlib):
+    """beta = 0: the SU(2) heatbath draws Haar links in one step; the SU(3)
+    pseudo-heatbath converges to Haar over a few steps."""
+    for nc, steps in [(2, 1), (3, 8)]:
+        with sunlib.Lattice(nc, (8, 8, 8, 8), 0.0, hot_start=False, seed=3) as L:
+            L.sweep(steps, 0)
+            U = L.export_links()
+        tr = np.trace(U.reshape(-1, nc, nc), axis1=1, axis2=2)
+        n = len(tr)
+        assert abs(tr.mean()) < 5 / np.sqrt(n)
+        assert abs((np.abs(tr) ** 2).mean() - 1) < 5 * np.sqrt(2.0 / n)
+
+
+def test_vanishing_staple_leaves_the_link(sunlib):
+    """SU(2): with U_mu(x - nu) = -1 for every nu != mu and all else 1, the
+    forward and backward staple terms cancel (Sigma = 0): both sides skip it."""
+    dims = (4, 4, 4, 4)
+    nx, ny, nz, nt = dims
+    U = orc.init(2, dims, False, 1)
+    mu = 0
+    x = (2, 2, 2, 2)  # even site
+    for nu in (1, 2, 3):
+        c = list(x)
+        c[nu] -= 1
+        U[mu, c[3], c[2], c[1], c[0]] = -np.eye(2)
+    for mode in (orc.HEATBATH, orc.OVERRELAX):
+        with gpu_lattice(sunlib, 2, dims, 4, 64, U) as L:
+            L.update_pass(mode, mu, 0)
+            got = L.export_links()
+        want = U.copy()
+        orc.update_pass(want, 2.3, mode, mu, 0, 0, 7)
+        assert np.array_equal(got[mu, 2, 2, 2, 2], np.eye(2))
+        assert maxdiff(got, want) < 1e-12
+
+
+def test_invalid_pass_arguments_raise(sunlib):
+    with sunlib.Lattice(2, (4, 4, 4, 4), 2.3) as L:
+        for args in [(2, 0, 0), (0, 4, 0), (0, 0, 2)]:
+            with pytest.raises(sunlib.SunError):
+                L.update_pass(*args)
+        with pytest.raises(sunlib.SunError):
+            L.heatbath_step = 2 ** 33

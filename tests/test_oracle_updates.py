@@ -242,12 +242,19 @@ def test_time_slab_passes_compose_to_a_full_pass():
 
 
 def test_beta_zero_heatbath_is_haar():
-    """beta = 0: the heatbath draws every link from the Haar measure whatever the
-    staple, so E Tr U = 0 and E|Tr U|^2 = 1."""
-    U = orc.init(3, (4, 4, 4, 4), hot=False, seed=1)
-    orc.sweep(U, 0.0, 1, 0, False, seed=9, hb_step0=0)
-    m = U.reshape(-1, 3, 3)
-    tr = np.trace(m, axis1=1, axis2=2)
-    n = len(tr)
-    assert abs(tr.mean()) < 5 / np.sqrt(n)
-    assert abs((np.abs(tr) ** 2).mean() - 1) < 5 * np.sqrt(2.0 / n)
+    """beta = 0: the SU(2) heatbath draws every link from the Haar measure in
+    one step, whatever the staple (E Tr U = 0, E|Tr U|^2 = 1); one
+    Cabibbo-Marinari step is not an exact SU(3) heatbath (E|Tr U|^2 < 1 from a
+    cold start) but repeated steps converge to Haar."""
+    for nc, steps, exact in [(2, 1, True), (3, 1, False), (3, 8, True)]:
+        U = orc.init(nc, (6, 6, 6, 6), hot=False, seed=1)
+        orc.sweep(U, 0.0, steps, 0, False, seed=9, hb_step0=0)
+        m = U.reshape(-1, nc, nc)
+        tr = np.trace(m, axis1=1, axis2=2)
+        n = len(tr)
+        assert abs(tr.mean()) < 5 / np.sqrt(n)
+        dev = abs((np.abs(tr) ** 2).mean() - 1)
+        if exact:
+            assert dev < 5 * np.sqrt(2.0 / n)
+        else:
+            assert dev > 5 * np.sqrt(2.0 / n)
