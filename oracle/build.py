@@ -19,7 +19,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest_src:
         return LIB
     cmd = ["gcc", "-std=gnu11", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-           "-fno-fast-math", "-Wall", "-Wextra", "-o", LIB + ".tmp"] + SOURCES + ["-lm"]
+           "-fno-fast-math", "-Wall", "-Wextra", "-Wno-maybe-uninitialized", "-o", LIB + ".tmp"] + SOURCES + ["-lm"]
     if verbose:
         print(" ".join(cmd), file=sys.stderr)
     subprocess.run(cmd, check=True)

@@ -32,6 +32,11 @@
  *       Gaussians (Box-Muller), i.e. a Haar-random SU(Nc) matrix.
  *   R10 plaquette normalised as sum_x sum_{mu<nu} ReTr P / (6 V Nc); Polyakov
  *       loop sum_xvec Tr prod_{t=0}^{Nt-1} U_3(xvec,t) / (Nc Nx Ny Nz).
+ *   R11 re-unitarization placement: after the heatbath and overrelaxation steps
+ *       of a sweep (Secs. 2-3), or, as a second schedule, each link right after
+ *       its update in the sweep's last step.  Either way every link is
+ *       re-unitarized once per sweep; in the second the later passes of that
+ *       step see re-unitarized neighbours.
  *
  * Floating point: compile with -ffp-contract=off and without -ffast-math.
  */
@@ -445,7 +450,7 @@ void orc_init(double* U, int nc, const int dims[4], int hot, uint64_t seed) {
  * Returns the number of subgroup heatbaths that reached the attempt cap. */
 int64_t orc_pass(double* U, int nc, const int dims[4], double beta, int mode, int mu,
                  int parity, uint32_t hb_step, uint64_t seed, int t_begin, int t_end,
-                 int reverse) {
+                 int reverse, int reunit_after) {
   int64_t V = volume(dims);
   int64_t per_t = (int64_t)dims[0] * dims[1] * dims[2];
   if (t_begin < 0) t_begin = 0;
@@ -460,6 +465,7 @@ int64_t orc_pass(double* U, int nc, const int dims[4], double beta, int mode, in
     orc_staple(U, nc, dims, mu, lex, (double*)S);
     capped += orc_update_link((double*)link_m(U, nc, V, mu, lex), (const double*)S, nc, beta,
                               mode, seed, (uint32_t)((int64_t)mu * V + lex), hb_step);
+    if (reunit_after) orc_reunit_link((double*)link_m(U, nc, V, mu, lex), nc);
   }
   return capped;
 }
@@ -472,18 +478,19 @@ void orc_reunitarize(double* U, int nc, const int dims[4]) {
 
 /* One sweep: n_hb heatbath steps (heatbath step counter hb_step0, hb_step0+1, ...),
  * then n_or overrelaxation steps, each step = 4 directions x (even, odd); then
- * optional re-unitarization. */
+ * re-unitarization as R11 (reunit = 0 none, 1 after the sweep, 2 in the last step). */
 void orc_sweep(double* U, int nc, const int dims[4], double beta, int n_hb, int n_or,
                int reunit, uint64_t seed, uint32_t hb_step0) {
-  for (int s = 0; s < n_hb; ++s)
+  int n_steps = n_hb + n_or;
+  for (int s = 0; s < n_steps; ++s) {
+    int heatbath = s < n_hb;
+    int fuse = (reunit == 2) && (s == n_steps - 1);
     for (int mu = 0; mu < 4; ++mu)
       for (int p = 0; p < 2; ++p)
-        orc_pass(U, nc, dims, beta, ORC_HEATBATH, mu, p, hb_step0 + (uint32_t)s, seed, 0, dims[3], 0);
-  for (int s = 0; s < n_or; ++s)
-    for (int mu = 0; mu < 4; ++mu)
-      for (int p = 0; p < 2; ++p)
-        orc_pass(U, nc, dims, beta, ORC_OVERRELAX, mu, p, 0, seed, 0, dims[3], 0);
-  if (reunit) orc_reunitarize(U, nc, dims);
+        orc_pass(U, nc, dims, beta, heatbath ? ORC_HEATBATH : ORC_OVERRELAX, mu, p,
+                 heatbath ? hb_step0 + (uint32_t)s : 0u, seed, 0, dims[3], 0, fuse);
+  }
+  if (reunit == 1 || (reunit == 2 && n_steps == 0)) orc_reunitarize(U, nc, dims);
 }
 
 /* Plaquette average, Eq. 4 with the normalisation of R10.  Partial sums per

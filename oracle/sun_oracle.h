@@ -47,7 +47,9 @@ double orc_uniform(uint32_t u);
 void orc_init(double* U, int nc, const int dims[4], int hot, uint64_t seed);
 int64_t orc_pass(double* U, int nc, const int dims[4], double beta, int mode, int mu,
                  int parity, uint32_t hb_step, uint64_t seed, int t_begin, int t_end,
-                 int reverse);
+                 int reverse, int reunit_after);
+/* reunit: 0 none, 1 every link after the sweep (Sec. 2/3 placement), 2 each link
+ * right after its update in the sweep's last step */
 void orc_sweep(double* U, int nc, const int dims[4], double beta, int n_hb, int n_or,
                int reunit, uint64_t seed, uint32_t hb_step0);
 void orc_reunitarize(double* U, int nc, const int dims[4]);

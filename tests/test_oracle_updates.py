@@ -258,3 +258,29 @@ def test_beta_zero_heatbath_is_haar():
             assert dev < 5 * np.sqrt(2.0 / n)
         else:
             assert dev > 5 * np.sqrt(2.0 / n)
+
+
+@pytest.mark.parametrize("nc", [2, 3, 4])
+def test_fused_reunitarization_schedule(nc):
+    """The fused schedule re-unitarizes every link once per sweep (all links
+    special unitary afterwards) and differs from the separate placement only
+    at the level of the unitarity drift it removes."""
+    beta = 2.3 if nc == 2 else 0.7 * nc * nc
+    U = random_gauge_config(nc, (4, 2, 4, 4), seed=800 + nc)
+    rng = np.random.default_rng(nc)
+    U = U + 1e-9 * (rng.normal(size=U.shape) + 1j * rng.normal(size=U.shape))  # small drift
+    A, B = U.copy(), U.copy()
+    orc.sweep(A, beta, 1, 2, orc.REUNIT_AFTER, 4, 0)
+    orc.sweep(B, beta, 1, 2, orc.REUNIT_FUSED, 4, 0)
+    for X in (A, B):
+        m = X.reshape(-1, nc, nc)
+        assert np.abs(m @ dag(m) - np.eye(nc)).max() < 1e-14
+        assert np.abs(np.linalg.det(m) - 1).max() < 1e-14
+    assert 0 < np.abs(A - B).max() < 1e-6
+    # with the last step's pass order, fused = pass then reunit link by link
+    C = U.copy()
+    orc.sweep(C, beta, 1, 1, orc.REUNIT_NONE, 4, 0)
+    for mu in range(4):
+        for p in range(2):
+            orc.update_pass(C, beta, orc.OVERRELAX, mu, p, 0, 4, reunit_after=True)
+    assert np.array_equal(C, B)
