@@ -28,8 +28,8 @@ MUTANTS = {
     # Kennedy-Pendleton rate alpha instead of 2 alpha
     "kp_rate": (r"/ \(2\.0 \* alpha\);", "/ alpha;"),
     # Creutz inversion with the wrong scale
-    "creutz_scale": (r"double x = 1\.0 \+ log1p\(-r\[0\] \* e\) / alpha;",
-                     "double x = 1.0 + log1p(-r[0] * e) / (2.0 * alpha);"),
+    "creutz_scale": (r"1\.0 \+ log1p\(-r\[0\] \* e\) / alpha :",
+                     "1.0 + log1p(-r[0] * e) / (2.0 * alpha) :"),
     # plaquette with U_nu(x+mu)^+ in place of U_mu(x+nu)^+
     "plaquette_swapped_link": (r"mat_dag\(nc, link_c\(U, nc, V, mu, hop\(dims, lex, nu, \+1\)\), D\);",
                                "mat_dag(nc, link_c(U, nc, V, nu, hop(dims, lex, mu, +1)), D);"),
