@@ -37,7 +37,7 @@ def lib():
         L.orc_init.argtypes = [d, ctypes.c_int, i4, ctypes.c_int, ctypes.c_uint64]
         L.orc_pass.argtypes = [d, ctypes.c_int, i4, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int,
-                               ctypes.c_int, ctypes.c_int, ctypes.c_int]
+                               ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.orc_pass.restype = ctypes.c_int64
         L.orc_sweep.argtypes = [d, ctypes.c_int, i4, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                 ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32]
@@ -99,19 +99,24 @@ def init(nc, dims, hot, seed):
 
 
 def update_pass(U, beta, mode, mu, parity, hb_step, seed, t_begin=0, t_end=-1, reverse=False,
-                reunit_after=False):
+                reunit_after=False, reunit_mod=0, reunit_rem=0):
+    """reunit_after re-unitarizes every updated link; reunit_mod/reunit_rem select
+    runs of 32 even/odd site indices ((lex >> 1) >> 5) % reunit_mod == reunit_rem."""
     nc = U.shape[-1]
     dims = (U.shape[4], U.shape[3], U.shape[2], U.shape[1])
+    if reunit_after:
+        reunit_mod, reunit_rem = 1, 0
     return lib().orc_pass(_dptr(U), nc, _dims(dims), float(beta), int(mode), int(mu), int(parity),
                           int(hb_step), int(seed), int(t_begin), int(t_end), int(bool(reverse)),
-                          int(bool(reunit_after)))
+                          int(reunit_mod), int(reunit_rem))
 
 
-REUNIT_NONE, REUNIT_AFTER, REUNIT_FUSED = 0, 1, 2
+REUNIT_NONE, REUNIT_AFTER, REUNIT_FUSED, REUNIT_SPREAD = 0, 1, 2, 3
 
 
 def sweep(U, beta, n_hb, n_or, reunit, seed, hb_step0):
-    """reunit: False/0 none, True/1 after the sweep, 2 fused into the last step."""
+    """reunit: False/0 none, True/1 after the sweep, 2 fused into the last step,
+    3 spread over the steps (runs of 32 links)."""
     nc = U.shape[-1]
     dims = (U.shape[4], U.shape[3], U.shape[2], U.shape[1])
     lib().orc_sweep(_dptr(U), nc, _dims(dims), float(beta), int(n_hb), int(n_or),

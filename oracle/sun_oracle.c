@@ -33,10 +33,11 @@
  *   R10 plaquette normalised as sum_x sum_{mu<nu} ReTr P / (6 V Nc); Polyakov
  *       loop sum_xvec Tr prod_{t=0}^{Nt-1} U_3(xvec,t) / (Nc Nx Ny Nz).
  *   R11 re-unitarization placement: after the heatbath and overrelaxation steps
- *       of a sweep (Secs. 2-3), or, as a second schedule, each link right after
- *       its update in the sweep's last step.  Either way every link is
- *       re-unitarized once per sweep; in the second the later passes of that
- *       step see re-unitarized neighbours.
+ *       of a sweep (Secs. 2-3); or each link right after its update in the
+ *       sweep's last step; or spread over the steps, links grouped in runs of 32
+ *       consecutive even/odd site indices (lex >> 1) and run r re-unitarized
+ *       right after its update in step r mod (number of steps).  In every
+ *       schedule each link is re-unitarized once per sweep.
  *
  * Floating point: compile with -ffp-contract=off and without -ffast-math.
  */
@@ -450,7 +451,7 @@ void orc_init(double* U, int nc, const int dims[4], int hot, uint64_t seed) {
  * Returns the number of subgroup heatbaths that reached the attempt cap. */
 int64_t orc_pass(double* U, int nc, const int dims[4], double beta, int mode, int mu,
                  int parity, uint32_t hb_step, uint64_t seed, int t_begin, int t_end,
-                 int reverse, int reunit_after) {
+                 int reverse, int reunit_mod, int reunit_rem) {
   int64_t V = volume(dims);
   int64_t per_t = (int64_t)dims[0] * dims[1] * dims[2];
   if (t_begin < 0) t_begin = 0;
@@ -465,7 +466,8 @@ int64_t orc_pass(double* U, int nc, const int dims[4], double beta, int mode, in
     orc_staple(U, nc, dims, mu, lex, (double*)S);
     capped += orc_update_link((double*)link_m(U, nc, V, mu, lex), (const double*)S, nc, beta,
                               mode, seed, (uint32_t)((int64_t)mu * V + lex), hb_step);
-    if (reunit_after) orc_reunit_link((double*)link_m(U, nc, V, mu, lex), nc);
+    if (reunit_mod > 0 && ((lex >> 1) >> 5) % reunit_mod == reunit_rem)
+      orc_reunit_link((double*)link_m(U, nc, V, mu, lex), nc);
   }
   return capped;
 }
@@ -478,19 +480,25 @@ void orc_reunitarize(double* U, int nc, const int dims[4]) {
 
 /* One sweep: n_hb heatbath steps (heatbath step counter hb_step0, hb_step0+1, ...),
  * then n_or overrelaxation steps, each step = 4 directions x (even, odd); then
- * re-unitarization as R11 (reunit = 0 none, 1 after the sweep, 2 in the last step). */
+ * re-unitarization as R11 (reunit = 0 none, 1 after the sweep, 2 in the last
+ * step, 3 spread over the steps). */
 void orc_sweep(double* U, int nc, const int dims[4], double beta, int n_hb, int n_or,
                int reunit, uint64_t seed, uint32_t hb_step0) {
   int n_steps = n_hb + n_or;
   for (int s = 0; s < n_steps; ++s) {
     int heatbath = s < n_hb;
-    int fuse = (reunit == 2) && (s == n_steps - 1);
+    int mod = 0, rem = 0;
+    if (reunit == 2 && s == n_steps - 1) mod = 1;
+    if (reunit == 3) {
+      mod = n_steps;
+      rem = s;
+    }
     for (int mu = 0; mu < 4; ++mu)
       for (int p = 0; p < 2; ++p)
         orc_pass(U, nc, dims, beta, heatbath ? ORC_HEATBATH : ORC_OVERRELAX, mu, p,
-                 heatbath ? hb_step0 + (uint32_t)s : 0u, seed, 0, dims[3], 0, fuse);
+                 heatbath ? hb_step0 + (uint32_t)s : 0u, seed, 0, dims[3], 0, mod, rem);
   }
-  if (reunit == 1 || (reunit == 2 && n_steps == 0)) orc_reunitarize(U, nc, dims);
+  if (reunit == 1 || (reunit >= 2 && n_steps == 0)) orc_reunitarize(U, nc, dims);
 }
 
 /* Plaquette average, Eq. 4 with the normalisation of R10.  Partial sums per

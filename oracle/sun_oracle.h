@@ -45,11 +45,15 @@ double orc_uniform(uint32_t u);
 
 /* Lattice-wide operations (U in canonical order, dims = {Nx,Ny,Nz,Nt}). */
 void orc_init(double* U, int nc, const int dims[4], int hot, uint64_t seed);
+/* reunit_mod > 0: after its update, link U_mu(x) is re-unitarized when
+ * ((lex >> 1) >> 5) % reunit_mod == reunit_rem (runs of 32 consecutive even/odd
+ * site indices); reunit_mod = 1, reunit_rem = 0 selects every link */
 int64_t orc_pass(double* U, int nc, const int dims[4], double beta, int mode, int mu,
                  int parity, uint32_t hb_step, uint64_t seed, int t_begin, int t_end,
-                 int reverse, int reunit_after);
+                 int reverse, int reunit_mod, int reunit_rem);
 /* reunit: 0 none, 1 every link after the sweep (Sec. 2/3 placement), 2 each link
- * right after its update in the sweep's last step */
+ * right after its update in the sweep's last step, 3 each run r of 32 links right
+ * after its update in step r mod (n_hb + n_or) */
 void orc_sweep(double* U, int nc, const int dims[4], double beta, int n_hb, int n_or,
                int reunit, uint64_t seed, uint32_t hb_step0);
 void orc_reunitarize(double* U, int nc, const int dims[4]);

@@ -284,3 +284,32 @@ def test_fused_reunitarization_schedule(nc):
         for p in range(2):
             orc.update_pass(C, beta, orc.OVERRELAX, mu, p, 0, 4, reunit_after=True)
     assert np.array_equal(C, B)
+
+
+@pytest.mark.parametrize("nc", [2, 3])
+def test_spread_reunitarization_schedule(nc):
+    """Spread schedule: every link re-unitarized once per sweep, in the step
+    given by its run of 32 site indices; a link re-unitarized in step s then
+    takes the remaining updates of the sweep, so the drift left is that of at
+    most n_steps - 1 updates."""
+    beta = 2.3 if nc == 2 else 6.0
+    dims = (8, 8, 4, 4)
+    U = random_gauge_config(nc, dims, seed=850 + nc)
+    rng = np.random.default_rng(nc)
+    drift = U + 1e-6 * (rng.normal(size=U.shape) + 1j * rng.normal(size=U.shape))
+    A = drift.copy()
+    orc.sweep(A, beta, 1, 2, orc.REUNIT_SPREAD, 4, 0)
+    m = A.reshape(-1, nc, nc)
+    assert np.abs(m @ dag(m) - np.eye(nc)).max() < 1e-12
+    # pass by pass it is the same thing
+    B = drift.copy()
+    for s, mode in enumerate([orc.HEATBATH, orc.OVERRELAX, orc.OVERRELAX]):
+        for mu in range(4):
+            for p in range(2):
+                orc.update_pass(B, beta, mode, mu, p, 0, 4, reunit_mod=3, reunit_rem=s)
+    assert np.array_equal(A, B)
+    # and without any re-unitarization the 1e-6 drift survives
+    C = drift.copy()
+    orc.sweep(C, beta, 1, 2, orc.REUNIT_NONE, 4, 0)
+    m = C.reshape(-1, nc, nc)
+    assert np.abs(m @ dag(m) - np.eye(nc)).max() > 1e-7
