@@ -4,8 +4,10 @@
 Workload (the configuration the %-of-HBM metric is quoted on): SU(3) on a
 48^3 x 96 lattice, beta = 6.2, cold start, sweeps of 1 heatbath + 5
 overrelaxation steps (each step = 8 chessboard passes), FP32 links in two-row
-(12-real) storage, FP64 reunitarization, plaquette and Polyakov loop measured
-after every sweep.  One benchmark step = one such sweep (the whole hot path).
+(12-real) storage, FP64 reunitarization of every link once per sweep (inside
+the update kernels of the sweep's last step), plaquette and Polyakov loop
+measured after every sweep.  One benchmark step = one such sweep (the whole
+hot path).
 
   value      link updates/s, device-resident lattice (2.0 GB, larger than L2),
              CUDA events on the lattice's stream, max over ranks
@@ -253,7 +255,8 @@ def gpu_arm(args):
     hbm_peak, peak_kind = measured_peaks()
 
     # ---- headline: FP32, two-row storage
-    L = sun.Lattice(NC, DIMS, BETA, hot_start=False, seed=1 + rank, precision=32, storage=args.storage)
+    kw = dict(precision=32, reunit_mode=args.reunit_mode, variant=args.variant)
+    L = sun.Lattice(NC, DIMS, BETA, hot_start=False, seed=1 + rank, storage=args.storage, **kw)
     L.run(W, N_HB, N_OR)
     barrier(world)
     torch.cuda.synchronize()
@@ -274,25 +277,35 @@ def gpu_arm(args):
     kernel_tag = f"or_pass_su3_{args.storage}real_fp32_48x48x48x96"
     traffic = profiled_traffic(kernel_tag)
 
-    # ---- FP32 full (18-real) storage, for the storage comparison
+    # ---- the other storage format, and the two-row staple products (variant bit 2)
     variants = {}
     if not args.no_variants:
-        alt = 18 if args.storage == 12 else 12
         L.close()
         del L
         torch.cuda.empty_cache()
-        L2 = sun.Lattice(NC, DIMS, BETA, hot_start=False, seed=1 + rank, precision=32, storage=alt)
-        L2.run(max(1, W // 2), N_HB, N_OR)
-        ms2, _, _ = run_sweeps(L2, max(2, K // 2))
-        k2 = time_kernel(L2, 16)
-        variants[f"fp32_{alt}real"] = {
-            "value": updates_per_sweep() * max(2, K // 2) / (ms2 / 1e3), "unit": METRIC,
-            "ms_per_step": ms2 / max(2, K // 2), "or_pass_ms": k2,
-            "or_pass_gbs": (V // 2) * 9 * L2.link_bytes / (k2 / 1e3) / 1e9}
-        L2.close()
-        del L2
-        torch.cuda.empty_cache()
-        L = sun.Lattice(NC, DIMS, BETA, hot_start=False, seed=1 + rank, precision=32, storage=args.storage)
+        alt = 18 if args.storage == 12 else 12
+        for name, st, var in [(f"fp32_{alt}real", alt, args.variant),
+                              ("fp32_12real_two_row_staple", 12, args.variant | 2)]:
+            if st == args.storage and var == args.variant:
+                continue
+            L2 = sun.Lattice(NC, DIMS, BETA, hot_start=False, seed=1 + rank, storage=st,
+                             **dict(kw, variant=var))
+            L2.run(max(1, W // 2), N_HB, N_OR)
+            k2s = max(2, K // 2)
+            ms2, _, _ = run_sweeps(L2, k2s)
+            k2 = time_kernel(L2, 16)
+            variants[name] = {
+                "value": updates_per_sweep() * k2s / (ms2 / 1e3), "unit": METRIC, "storage_reals": st,
+                "variant": var, "ms_per_step": ms2 / k2s, "or_pass_ms": k2,
+                "or_pass_gbs": (V // 2) * 9 * L2.link_bytes / (k2 / 1e3) / 1e9}
+            if var & 2:
+                variants[name]["note"] = ("third row of each staple term taken as conj(row0 x row1): "
+                                          "up to 1.2e-5 from the oracle on links of a Haar start before "
+                                          "their first re-unitarization (1e-5 bar)")
+            L2.close()
+            del L2
+            torch.cuda.empty_cache()
+        L = sun.Lattice(NC, DIMS, BETA, hot_start=False, seed=1 + rank, storage=args.storage, **kw)
 
     # ---- end to end through the C ABI with pinned host buffers
     e2e = None
@@ -346,7 +359,11 @@ def gpu_arm(args):
         "data": "synthetic (cold start, Philox seed 1 + rank)",
         "config": {"workload": WORKLOAD_NAME, "nc": NC, "dims": list(DIMS), "beta": BETA,
                    "n_heatbath": N_HB, "n_overrelax": N_OR, "storage_reals": args.storage,
-                   "reunitarize": "FP64 every sweep", "observables": "FP64 plaquette + Polyakov every sweep",
+                   "kernel_variant": args.variant,
+                   "reunitarize": ("FP64, every link once per sweep, " +
+                                   {0: "own pass after the sweep", 1: "in the update kernels of the last step",
+                                    2: "spread over the steps"}[args.reunit_mode]),
+                   "observables": "FP64 plaquette + Polyakov every sweep",
                    "link_updates_per_step": updates_per_sweep(),
                    "l2": "lattice (2.0 GB) larger than L2, no flush", "parallelism": f"replicas x{world}"},
         "hbm_gbs_effective": updates_per_sweep() * 9 * link_bytes / (ms_max / K / 1e3) / 1e9,
@@ -354,7 +371,7 @@ def gpu_arm(args):
         "polyakov_last": [float(poly[-1].real), float(poly[-1].imag)],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": traffic,
-                     "kernel": "update_pass_mat<float,3,two-row,overrelax>",
+                     "kernel": "update_pass_mat_occ<float,3,two-row,overrelax,variant 1>",
                      "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": k_ms,
                      "peak_kind": peak_kind + " (hbm_gbs, copy kernel)"},
         "variants": variants,
@@ -402,6 +419,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--storage", type=int, default=12, choices=[12, 18])
+    ap.add_argument("--variant", type=int, default=1, choices=[0, 1, 2, 3],
+                    help="update-kernel variant bits: 1 = 6 blocks/SM register bound, 2 = two-row staple")
+    ap.add_argument("--reunit-mode", type=int, default=1, choices=[0, 1, 2])
     ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")

@@ -73,6 +73,21 @@ enum { SUN_HEATBATH = 0, SUN_OVERRELAX = 1 };
  *                it must be 256-byte aligned and outlive the lattice.  NULL = the
  *                library allocates (cudaMalloc) and frees.
  *  use_graphs    sun_run captures one sweep as a CUDA graph and replays it (default 1).
+ *  variant       update-pass kernel variant, bit flags (default 0), built for SU(3)
+ *                FP32 and ignored elsewhere: 1 = bound the registers for 6
+ *                resident 128-thread blocks per SM (same results); 2 = with
+ *                two-row storage, multiply out rows 0 and 1 of each staple term
+ *                only and take its third row as conj(row0 x row1), exact for SU(3)
+ *                products (results move by the order of the links' unitarity
+ *                drift, ~1e-6 between re-unitarizations).
+ *  reunit_mode   where a sweep re-unitarizes (default 0); every link is
+ *                re-unitarized once per re-unitarizing sweep in all three:
+ *                0 = all links after the sweep's last step, as a pass of its own
+ *                (the placement of Secs. 2-3); 1 = each link of the last step right
+ *                after its update, inside the update kernel; 2 = spread over the
+ *                steps: links in runs of 32 consecutive even/odd site indices
+ *                (lex >> 1), run r re-unitarized right after its update in step
+ *                r mod (n_heatbath + n_overrelax), inside the update kernel.
  */
 typedef struct {
   int precision;
@@ -83,6 +98,8 @@ typedef struct {
   void* device_buf;
   size_t device_buf_bytes;
   int use_graphs;
+  int variant;
+  int reunit_mode;
 } sun_options;
 
 int sun_abi_version(void);
@@ -138,8 +155,11 @@ sun_status sun_plaquette(sun_lattice* lat, double* out);
 sun_status sun_polyakov_loop(sun_lattice* lat, double* re, double* im);
 
 /* Copy all links to / from host memory in canonical order (n_doubles must equal
- * 8*Nc*Nc*V).  Export rebuilds the third row of 12-real storage; import of a
- * 12-real lattice keeps rows 0 and 1 only.  Both sync. */
+ * 8*Nc*Nc*V; the buffer 16-byte aligned).  Export rebuilds the third row of
+ * 12-real storage; import of a 12-real lattice keeps rows 0 and 1 only.
+ * Page-locked host memory is read or written directly by the conversion kernel
+ * (mapped into the device address space); pageable memory goes through a
+ * device staging buffer in chunks.  Both sync. */
 sun_status sun_export_links(sun_lattice* lat, double* host, size_t n_doubles);
 sun_status sun_import_links(sun_lattice* lat, const double* host, size_t n_doubles);
 

@@ -127,7 +127,7 @@ struct sun_lattice {
   int dims[4] = {0, 0, 0, 0};
   double beta = 0.0;
   uint64_t seed = 0;
-  int reunit_every = 1, block_threads = 128, use_graphs = 1;
+  int reunit_every = 1, reunit_mode = 0, block_threads = 128, use_graphs = 1;
   int device = 0;
   uint64_t sweeps_done = 0;
   cudaStream_t stream = nullptr;
@@ -174,15 +174,24 @@ sun_status check_launch(cudaError_t e, const char* what) {
 sun_status enqueue_sweep(sun_lattice* L, cudaStream_t s, int n_hb, int n_or, bool reunit, bool plaq,
                          bool poly, bool hist_mode) {
   const sun::Ctx c = ctx_on(L, s);
-  for (int step = 0; step < n_hb; ++step)
+  const int n_steps = n_hb + n_or;
+  // reunit_mode 1: every link of the last step re-unitarized in the update kernel;
+  // reunit_mode 2: runs of 32 links spread over the steps (run r in step r mod n_steps)
+  const bool fused = reunit && L->reunit_mode != 0 && n_steps > 0;
+  for (int step = 0; step < n_steps; ++step) {
+    const bool hb = step < n_hb;
+    uint32_t mod = 0, rem = 0;
+    if (fused && L->reunit_mode == 1 && step == n_steps - 1) mod = 1;
+    if (fused && L->reunit_mode == 2) {
+      mod = uint32_t(n_steps);
+      rem = uint32_t(step);
+    }
     for (int mu = 0; mu < 4; ++mu)
       for (int p = 0; p < 2; ++p)
-        SUN_TRY(check_launch(L->ops->pass(c, SUN_HEATBATH, mu, p, uint32_t(step)), "heatbath pass"));
-  for (int step = 0; step < n_or; ++step)
-    for (int mu = 0; mu < 4; ++mu)
-      for (int p = 0; p < 2; ++p)
-        SUN_TRY(check_launch(L->ops->pass(c, SUN_OVERRELAX, mu, p, 0u), "overrelaxation pass"));
-  if (reunit) SUN_TRY(check_launch(L->ops->reunit(c), "reunitarization"));
+        SUN_TRY(check_launch(L->ops->pass(c, hb ? SUN_HEATBATH : SUN_OVERRELAX, mu, p, hb ? uint32_t(step) : 0u, mod, rem),
+                             hb ? "heatbath pass" : "overrelaxation pass"));
+  }
+  if (reunit && !fused) SUN_TRY(check_launch(L->ops->reunit(c), "reunitarization"));
   const uint32_t* slot = hist_mode ? &L->ctx.state->slot : nullptr;
   if (plaq) SUN_TRY(check_launch(L->ops->plaquette(c, hist_mode ? L->hist : L->results, slot, kHistCap), "plaquette"));
   if (poly)
@@ -247,6 +256,8 @@ void sun_options_init(sun_options* opt) {
   opt->device_buf = nullptr;
   opt->device_buf_bytes = 0;
   opt->use_graphs = 1;
+  opt->variant = 0;
+  opt->reunit_mode = 0;
 }
 
 const char* sun_status_string(sun_status s) {
@@ -276,6 +287,9 @@ static sun_status resolve(int nc, const int* dims, const sun_options* opt_in, su
   if (opt->storage == 0) opt->storage = default_storage(nc);
   if (opt->reunit_every < 0) return fail(SUN_ERR_ARG, "reunit_every must be >= 0");
   if (opt->block_threads == 0) opt->block_threads = 128;
+  if (opt->variant < 0 || opt->variant > 3) return fail(SUN_ERR_ARG, "variant = %d must be in 0..3", opt->variant);
+  if (opt->reunit_mode < 0 || opt->reunit_mode > 2)
+    return fail(SUN_ERR_ARG, "reunit_mode = %d must be 0, 1 or 2", opt->reunit_mode);
   if (opt->block_threads < 32 || opt->block_threads > 256 || (opt->block_threads & 31))
     return fail(SUN_ERR_ARG, "block_threads = %d must be a multiple of 32 in [32, 256]", opt->block_threads);
   *ops = find_ops(nc, opt->storage, opt->precision);
@@ -309,6 +323,7 @@ sun_status sun_lattice_create(sun_lattice** out, int nc, const int dims[4], doub
   L->beta = beta;
   L->seed = seed;
   L->reunit_every = opt.reunit_every;
+  L->reunit_mode = opt.reunit_mode;
   L->block_threads = opt.block_threads;
   L->use_graphs = opt.use_graphs;
   L->ops = ops;
@@ -364,6 +379,10 @@ sun_status sun_lattice_create(sun_lattice** out, int nc, const int dims[4], doub
   g.stride[1] = dims[0];
   g.stride[2] = int64_t(dims[0]) * dims[1];
   g.stride[3] = int64_t(dims[0]) * dims[1] * dims[2];
+  g.div_nxh = sun::make_fastdiv(uint32_t(g.nxh));
+  g.div_ny = sun::make_fastdiv(uint32_t(g.ny));
+  g.div_nz = sun::make_fastdiv(uint32_t(g.nz));
+  g.div_nx = sun::make_fastdiv(uint32_t(g.nx));
 
   sun::Ctx& c = L->ctx;
   c.links = L->base + L->plan.links_off;
@@ -376,6 +395,7 @@ sun_status sun_lattice_create(sun_lattice** out, int nc, const int dims[4], doub
   c.partials = reinterpret_cast<double*>(L->base + L->plan.partials_off);
   c.stream = L->stream;
   c.block_threads = L->block_threads;
+  c.variant = opt.variant;
   int rb = 2 * (sms > 0 ? sms : 132);
   c.reduce_blocks = rb > sun::kMaxReduceBlocks ? sun::kMaxReduceBlocks : rb;
   L->results = reinterpret_cast<double*>(L->base + L->plan.results_off);
@@ -408,7 +428,7 @@ sun_status sun_update_pass(sun_lattice* L, int mode, int mu, int parity) {
   if (mu < 0 || mu > 3) return fail(SUN_ERR_ARG, "mu must be in 0..3");
   if (parity != 0 && parity != 1) return fail(SUN_ERR_ARG, "parity must be 0 or 1");
   SUN_TRY(set_device(L));
-  return check_launch(L->ops->pass(ctx_on(L, L->stream), mode, mu, parity, 0u), "update pass");
+  return check_launch(L->ops->pass(ctx_on(L, L->stream), mode, mu, parity, 0u, 0u, 0u), "update pass");
 }
 
 sun_status sun_sweep(sun_lattice* L, int n_hb, int n_or) {
@@ -477,17 +497,35 @@ sun_status sun_polyakov_loop(sun_lattice* L, double* re, double* im) {
 
 static size_t canonical_doubles(const sun_lattice* L) { return size_t(8) * L->nc * L->nc * size_t(L->ctx.g.V); }
 
+// Device address of page-locked host memory (mapped into the device address
+// space), or NULL for pageable memory.  Conversion kernels then read or write
+// the host buffer directly; otherwise they go through the staging buffer.
+static double* mapped_host(const void* host) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type == cudaMemoryTypeHost && a.devicePointer) return static_cast<double*>(a.devicePointer);
+  return nullptr;
+}
+
 sun_status sun_export_links(sun_lattice* L, double* host, size_t n) {
   if (!L || !host) return fail(SUN_ERR_ARG, "NULL argument");
   if (n != canonical_doubles(L)) return fail(SUN_ERR_ARG, "host buffer holds %zu doubles, need %zu", n, canonical_doubles(L));
+  if (reinterpret_cast<uintptr_t>(host) % 16) return fail(SUN_ERR_ARG, "host buffer must be 16-byte aligned");
   SUN_TRY(set_device(L));
   const sun::Ctx c = ctx_on(L, L->stream);
   const int64_t total = 4 * L->ctx.g.V, per = 2 * L->nc * L->nc;
-  for (int64_t first = 0; first < total; first += L->plan.staging_links) {
-    const int64_t cnt = (total - first) < L->plan.staging_links ? (total - first) : L->plan.staging_links;
-    SUN_TRY(check_launch(L->ops->export_links(c, L->staging, first, cnt), "export"));
-    SUN_CUDA(cudaMemcpyAsync(host + first * per, L->staging, size_t(cnt * per) * sizeof(double),
-                             cudaMemcpyDeviceToHost, L->stream));
+  if (double* dev = mapped_host(host)) {
+    SUN_TRY(check_launch(L->ops->export_links(c, dev, 0, total), "export"));
+  } else {
+    for (int64_t first = 0; first < total; first += L->plan.staging_links) {
+      const int64_t cnt = (total - first) < L->plan.staging_links ? (total - first) : L->plan.staging_links;
+      SUN_TRY(check_launch(L->ops->export_links(c, L->staging, first, cnt), "export"));
+      SUN_CUDA(cudaMemcpyAsync(host + first * per, L->staging, size_t(cnt * per) * sizeof(double),
+                               cudaMemcpyDeviceToHost, L->stream));
+    }
   }
   SUN_CUDA(cudaStreamSynchronize(L->stream));
   return SUN_OK;
@@ -496,14 +534,19 @@ sun_status sun_export_links(sun_lattice* L, double* host, size_t n) {
 sun_status sun_import_links(sun_lattice* L, const double* host, size_t n) {
   if (!L || !host) return fail(SUN_ERR_ARG, "NULL argument");
   if (n != canonical_doubles(L)) return fail(SUN_ERR_ARG, "host buffer holds %zu doubles, need %zu", n, canonical_doubles(L));
+  if (reinterpret_cast<uintptr_t>(host) % 16) return fail(SUN_ERR_ARG, "host buffer must be 16-byte aligned");
   SUN_TRY(set_device(L));
   const sun::Ctx c = ctx_on(L, L->stream);
   const int64_t total = 4 * L->ctx.g.V, per = 2 * L->nc * L->nc;
-  for (int64_t first = 0; first < total; first += L->plan.staging_links) {
-    const int64_t cnt = (total - first) < L->plan.staging_links ? (total - first) : L->plan.staging_links;
-    SUN_CUDA(cudaMemcpyAsync(L->staging, host + first * per, size_t(cnt * per) * sizeof(double),
-                             cudaMemcpyHostToDevice, L->stream));
-    SUN_TRY(check_launch(L->ops->import_links(c, L->staging, first, cnt), "import"));
+  if (const double* dev = mapped_host(host)) {
+    SUN_TRY(check_launch(L->ops->import_links(c, dev, 0, total), "import"));
+  } else {
+    for (int64_t first = 0; first < total; first += L->plan.staging_links) {
+      const int64_t cnt = (total - first) < L->plan.staging_links ? (total - first) : L->plan.staging_links;
+      SUN_CUDA(cudaMemcpyAsync(L->staging, host + first * per, size_t(cnt * per) * sizeof(double),
+                               cudaMemcpyHostToDevice, L->stream));
+      SUN_TRY(check_launch(L->ops->import_links(c, L->staging, first, cnt), "import"));
+    }
   }
   SUN_CUDA(cudaStreamSynchronize(L->stream));
   return SUN_OK;

@@ -447,16 +447,22 @@ struct Site {
   int64_t lex;
 };
 
-__device__ __forceinline__ Site decode_half(const Geom& g, int64_t h, int parity) {
+__device__ __forceinline__ uint32_t fdiv(const FastDiv& f, uint32_t n) {
+  return (__umulhi(n, f.m) + n) >> f.s;
+}
+
+__device__ __forceinline__ Site decode_half(const Geom& g, int64_t h64, int parity) {
   Site s;
-  int64_t rest = h / g.nxh;
-  const int xh = int(h - rest * g.nxh);
-  s.c[1] = int(rest % g.ny);
-  rest /= g.ny;
-  s.c[2] = int(rest % g.nz);
-  s.c[3] = int(rest / g.nz);
-  s.c[0] = 2 * xh + ((parity + s.c[1] + s.c[2] + s.c[3]) & 1);
-  s.lex = 2 * h + (s.c[0] & 1);
+  const uint32_t h = uint32_t(h64);
+  const uint32_t r1 = fdiv(g.div_nxh, h);
+  const uint32_t xh = h - r1 * uint32_t(g.nxh);
+  const uint32_t r2 = fdiv(g.div_ny, r1);
+  s.c[1] = int(r1 - r2 * uint32_t(g.ny));
+  const uint32_t t = fdiv(g.div_nz, r2);
+  s.c[2] = int(r2 - t * uint32_t(g.nz));
+  s.c[3] = int(t);
+  s.c[0] = int(2 * xh) + ((parity + s.c[1] + s.c[2] + s.c[3]) & 1);
+  s.lex = 2 * int64_t(h) + (s.c[0] & 1);
   return s;
 }
 

@@ -5,6 +5,8 @@
 // instantiates the table entries it needs.
 #pragma once
 
+#include <type_traits>
+
 #include "sun_device.cuh"
 
 namespace sun {
@@ -13,18 +15,19 @@ constexpr int kMaxBlockThreads = 256;
 constexpr int kHeatbathMode = 0;
 constexpr int kOverrelaxMode = 1;
 
-__device__ __forceinline__ int64_t stride_of(const Geom& g, int d) {
-  return d == 0 ? g.stride[0] : (d == 1 ? g.stride[1] : (d == 2 ? g.stride[2] : g.stride[3]));
+__device__ __forceinline__ uint32_t stride_of(const Geom& g, int d) {
+  return uint32_t(d == 0 ? g.stride[0] : (d == 1 ? g.stride[1] : (d == 2 ? g.stride[2] : g.stride[3])));
 }
-__device__ __forceinline__ int64_t fwd(const Geom& g, int64_t lex, int coord, int d) {
+// lex of the neighbour one step forward / backward along d (coord = the site's coordinate along d)
+__device__ __forceinline__ uint32_t fwd(const Geom& g, uint32_t lex, int coord, int d) {
   const int n = dim_of(g, d);
-  const int64_t st = stride_of(g, d);
-  return coord == n - 1 ? lex - int64_t(n - 1) * st : lex + st;
+  const uint32_t st = stride_of(g, d);
+  return coord == n - 1 ? lex - uint32_t(n - 1) * st : lex + st;
 }
-__device__ __forceinline__ int64_t bwd(const Geom& g, int64_t lex, int coord, int d) {
+__device__ __forceinline__ uint32_t bwd(const Geom& g, uint32_t lex, int coord, int d) {
   const int n = dim_of(g, d);
-  const int64_t st = stride_of(g, d);
-  return coord == 0 ? lex + int64_t(n - 1) * st : lex - st;
+  const uint32_t st = stride_of(g, d);
+  return coord == 0 ? lex + uint32_t(n - 1) * st : lex - st;
 }
 
 struct PassParams {
@@ -36,7 +39,14 @@ struct PassParams {
   uint2 key;
   const uint32_t* hb_step;
   uint32_t step_offset;
+  // FP64 re-unitarization right after the update of the links whose run of 32
+  // half-site indices r = h >> 5 has r % reunit_mod == reunit_rem (0 = none)
+  uint32_t reunit_mod, reunit_rem;
 };
+
+__device__ __forceinline__ bool reunit_selected(const PassParams& p, int64_t h) {
+  return p.reunit_mod != 0u && ((uint32_t(h) >> 5) % p.reunit_mod) == p.reunit_rem;
+}
 
 __device__ __forceinline__ const char* block_ptr(const PassParams& p, int d, int par) {
   return p.links + (2 * d + par) * p.block_bytes;
@@ -58,141 +68,6 @@ __device__ __forceinline__ void apply_rows(Mat<R, N>& m, int i, int j, const Qua
 }
 
 // ---------------------------------------------------------------------------
-// One chessboard pass over matrices (Nc >= 2, full or two-row storage):
-// staple (Eq. 9) -> W = U Sigma^+ -> SU(2) subgroups in lexicographic order
-// (Eq. 15), heatbath (Eqs. 12-14) or overrelaxation (Eq. 17) -> store.
-// One thread per link of the pass.
-// ---------------------------------------------------------------------------
-template <class R, int N, int S, int MODE>
-__global__ void __launch_bounds__(kMaxBlockThreads) update_pass_mat(const PassParams p) {
-  const int64_t h = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  const Geom& g = p.g;
-  if (h >= g.Vh) return;
-  const int mu = p.mu, par = p.parity, opp = par ^ 1;
-  const Site s = decode_half(g, h, par);
-  const int cmu = coord_of(s, mu);
-  const int64_t lex_pmu = fwd(g, s.lex, cmu, mu);
-
-  Mat<R, N> st;
-  mat_zero(st);
-#pragma unroll
-  for (int nu = 0; nu < 4; ++nu) {
-    if (nu == mu) continue;
-    const int cnu = s.c[nu];
-    const int64_t lex_pnu = fwd(g, s.lex, cnu, nu);
-    const int64_t lex_mnu = bwd(g, s.lex, cnu, nu);
-    const int64_t lex_mnu_pmu = fwd(g, lex_mnu, cmu, mu);
-    {  // U_nu(x) U_mu(x+nu) U_nu(x+mu)^+
-      const Mat<R, N> a = load_mat<R, N, S>(block_ptr(p, nu, par), g.Vh, h);
-      const Mat<R, N> b = load_mat<R, N, S>(block_ptr(p, mu, opp), g.Vh, lex_pnu >> 1);
-      const Mat<R, N> t = mul_nn(a, b);
-      const Mat<R, N> c = load_mat<R, N, S>(block_ptr(p, nu, opp), g.Vh, lex_pmu >> 1);
-      acc_nd(st, t, c);
-    }
-    {  // U_nu(x-nu)^+ U_mu(x-nu) U_nu(x-nu+mu)
-      const Mat<R, N> a = load_mat<R, N, S>(block_ptr(p, nu, opp), g.Vh, lex_mnu >> 1);
-      const Mat<R, N> b = load_mat<R, N, S>(block_ptr(p, mu, opp), g.Vh, lex_mnu >> 1);
-      const Mat<R, N> t = mul_dn(a, b);
-      const Mat<R, N> c = load_mat<R, N, S>(block_ptr(p, nu, par), g.Vh, lex_mnu_pmu >> 1);
-      acc_nn(st, t, c);
-    }
-  }
-
-  char* ublk = p.links + (2 * mu + par) * p.block_bytes;
-  Mat<R, N> u = load_mat<R, N, S, false>(ublk, g.Vh, h);
-  Mat<R, N> w = mul_nd(u, st);
-
-  uint32_t step = 0;
-  if constexpr (MODE == kHeatbathMode) step = *p.hb_step + p.step_offset;
-  const uint32_t link_id = uint32_t(mu) * uint32_t(g.V) + uint32_t(s.lex);
-  const R alpha_coef = R(p.alpha_coef);
-
-  int sub = 0;
-#pragma unroll
-  for (int i = 0; i < N - 1; ++i) {
-#pragma unroll
-    for (int j = i + 1; j < N; ++j) {
-      const bool last = (i == N - 2) && (j == N - 1);
-      const Quat<R> v = block_to_quat(w.e[i][i], w.e[i][j], w.e[j][i], w.e[j][j]);
-      const R k = d_sqrt(v.a0 * v.a0 + v.a1 * v.a1 + v.a2 * v.a2 + v.a3 * v.a3);
-      if (k > R(1e-15) && d_isfinite(k)) {
-        const R inv = R(1) / k;
-        const Quat<R> vd = {v.a0 * inv, -v.a1 * inv, -v.a2 * inv, -v.a3 * inv};  // vhat^+
-        Quat<R> a;
-        bool apply = true;
-        if constexpr (MODE == kHeatbathMode) {
-          Quat<R> b;
-          apply = heatbath_su2<R>(alpha_coef * k, p.key, link_id, step, uint32_t(sub), b);
-          a = qmul(b, vd);
-        } else {
-          a = qmul(vd, vd);
-        }
-        if (apply) {
-          apply_rows(u, i, j, a);
-          if (!last) apply_rows(w, i, j, a);
-        }
-      }
-      ++sub;
-    }
-  }
-  store_mat<R, N, S>(ublk, g.Vh, h, u);
-}
-
-// ---------------------------------------------------------------------------
-// One chessboard pass for SU(2) stored as quaternions (Eq. 6): the same steps
-// with the staple kept in the real span of SU(2).
-// ---------------------------------------------------------------------------
-template <class R, int MODE>
-__global__ void __launch_bounds__(kMaxBlockThreads) update_pass_quat(const PassParams p) {
-  const int64_t h = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  const Geom& g = p.g;
-  if (h >= g.Vh) return;
-  const int mu = p.mu, par = p.parity, opp = par ^ 1;
-  const Site s = decode_half(g, h, par);
-  const int cmu = coord_of(s, mu);
-  const int64_t lex_pmu = fwd(g, s.lex, cmu, mu);
-
-  Quat<R> st = {R(0), R(0), R(0), R(0)};
-#pragma unroll
-  for (int nu = 0; nu < 4; ++nu) {
-    if (nu == mu) continue;
-    const int cnu = s.c[nu];
-    const int64_t lex_pnu = fwd(g, s.lex, cnu, nu);
-    const int64_t lex_mnu = bwd(g, s.lex, cnu, nu);
-    const int64_t lex_mnu_pmu = fwd(g, lex_mnu, cmu, mu);
-    {
-      const Quat<R> a = load_quat<R>(block_ptr(p, nu, par), g.Vh, h);
-      const Quat<R> b = load_quat<R>(block_ptr(p, mu, opp), g.Vh, lex_pnu >> 1);
-      const Quat<R> c = load_quat<R>(block_ptr(p, nu, opp), g.Vh, lex_pmu >> 1);
-      st = qadd(st, qmul(qmul(a, b), qdag(c)));
-    }
-    {
-      const Quat<R> a = load_quat<R>(block_ptr(p, nu, opp), g.Vh, lex_mnu >> 1);
-      const Quat<R> b = load_quat<R>(block_ptr(p, mu, opp), g.Vh, lex_mnu >> 1);
-      const Quat<R> c = load_quat<R>(block_ptr(p, nu, par), g.Vh, lex_mnu_pmu >> 1);
-      st = qadd(st, qmul(qmul(qdag(a), b), c));
-    }
-  }
-  char* ublk = p.links + (2 * mu + par) * p.block_bytes;
-  Quat<R> u = load_quat<R, false>(ublk, g.Vh, h);
-  const Quat<R> w = qmul(u, qdag(st));
-  const R k = d_sqrt(w.a0 * w.a0 + w.a1 * w.a1 + w.a2 * w.a2 + w.a3 * w.a3);
-  if (k > R(1e-15) && d_isfinite(k)) {
-    const R inv = R(1) / k;
-    const Quat<R> vd = {w.a0 * inv, -w.a1 * inv, -w.a2 * inv, -w.a3 * inv};
-    if constexpr (MODE == kHeatbathMode) {
-      const uint32_t step = *p.hb_step + p.step_offset;
-      const uint32_t link_id = uint32_t(mu) * uint32_t(g.V) + uint32_t(s.lex);
-      Quat<R> b;
-      if (heatbath_su2<R>(R(p.alpha_coef) * k, p.key, link_id, step, 0u, b)) u = qmul(qmul(b, vd), u);
-    } else {
-      u = qmul(qmul(vd, vd), u);
-    }
-  }
-  store_quat<R>(ublk, g.Vh, h, u);
-}
-
-// ---------------------------------------------------------------------------
 // FP64 re-unitarization of one matrix (Sec. 2).
 // ---------------------------------------------------------------------------
 template <int N>
@@ -200,7 +75,7 @@ __device__ __forceinline__ void normalise_row(Mat<double, N>& m, int r) {
   double s = 0.0;
 #pragma unroll
   for (int c = 0; c < N; ++c) s += m.e[r][c].re * m.e[r][c].re + m.e[r][c].im * m.e[r][c].im;
-  const double inv = 1.0 / sqrt(s);
+  const double inv = rsqrt(s);
 #pragma unroll
   for (int c = 0; c < N; ++c) {
     m.e[r][c].re *= inv;
@@ -303,6 +178,294 @@ __device__ __forceinline__ Mat<B, N> mat_cast(const Mat<A, N>& m) {
   return o;
 }
 
+// ---------------------------------------------------------------------------
+// Staple terms (Eq. 9).  With ROWS2 (SU(3) two-row storage, kernel variant bit
+// 1) only rows 0 and 1 of each term are multiplied out and the term's third row
+// is taken as conj(row0 x row1), which holds for an exact SU(3) product: a third
+// fewer products, at an extra error of the order of the links' unitarity drift.
+// ---------------------------------------------------------------------------
+template <class R>
+struct Rows2 {
+  Cpx<R> e[2][3];
+};
+
+template <class R>
+__device__ __forceinline__ Rows2<R> load_rows2(const char* blk, int64_t Vh, int64_t h) {
+  R r[12];
+  load_reals<R, 12, true>(blk, Vh, h, r);
+  Rows2<R> m;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) m.e[i][j] = {r[2 * (3 * i + j)], r[2 * (3 * i + j) + 1]};
+  return m;
+}
+
+// U_nu(x) U_mu(x+nu) U_nu(x+mu)^+ added to st
+template <class R, int N, int S, bool ROWS2>
+__device__ __forceinline__ void staple_forward(Mat<R, N>& st, const char* pa, int64_t ha, const char* pb, int64_t hb,
+                                               const char* pc, int64_t hc, int64_t Vh) {
+  if constexpr (S == kTwoRow && ROWS2) {
+    const Rows2<R> a = load_rows2<R>(pa, Vh, ha);
+    const Mat<R, 3> b = load_mat<R, 3, S>(pb, Vh, hb);
+    Cpx<R> ab[2][3];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        Cpx<R> x = cmul(a.e[i][0], b.e[0][j]);
+        cfma(x, a.e[i][1], b.e[1][j]);
+        cfma(x, a.e[i][2], b.e[2][j]);
+        ab[i][j] = x;
+      }
+    const Mat<R, 3> c = load_mat<R, 3, S>(pc, Vh, hc);
+    Mat<R, 3> t;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        Cpx<R> x = cmulc(ab[i][0], c.e[j][0]);
+        cfmac(x, ab[i][1], c.e[j][1]);
+        cfmac(x, ab[i][2], c.e[j][2]);
+        t.e[i][j] = x;
+      }
+    su3_third_row(t);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        st.e[i][j].re += t.e[i][j].re;
+        st.e[i][j].im += t.e[i][j].im;
+      }
+  } else {
+    const Mat<R, N> a = load_mat<R, N, S>(pa, Vh, ha);
+    const Mat<R, N> b = load_mat<R, N, S>(pb, Vh, hb);
+    const Mat<R, N> t = mul_nn(a, b);
+    const Mat<R, N> c = load_mat<R, N, S>(pc, Vh, hc);
+    acc_nd(st, t, c);
+  }
+}
+
+// U_nu(x-nu)^+ U_mu(x-nu) U_nu(x-nu+mu) added to st
+template <class R, int N, int S, bool ROWS2>
+__device__ __forceinline__ void staple_backward(Mat<R, N>& st, const char* pa, int64_t ha, const char* pb, int64_t hb,
+                                                const char* pc, int64_t hc, int64_t Vh) {
+  if constexpr (S == kTwoRow && ROWS2) {
+    const Rows2<R> a = load_rows2<R>(pa, Vh, ha);
+    // entries (2,0), (2,1) of the third row conj(row0 x row1) of a
+    Cpx<R> a20, a21;
+    {
+      const Cpx<R> p = cmul(a.e[0][1], a.e[1][2]), q = cmul(a.e[0][2], a.e[1][1]);
+      a20 = {p.re - q.re, -(p.im - q.im)};
+      const Cpx<R> u = cmul(a.e[0][2], a.e[1][0]), v = cmul(a.e[0][0], a.e[1][2]);
+      a21 = {u.re - v.re, -(u.im - v.im)};
+    }
+    const Mat<R, 3> b = load_mat<R, 3, S>(pb, Vh, hb);
+    // rows 0,1 of a^+ b: (a^+ b)_ik = sum_m conj(a_mi) b_mk
+    Cpx<R> d[2][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      Cpx<R> x = ccmul(a.e[0][0], b.e[0][k]);
+      ccfma(x, a.e[1][0], b.e[1][k]);
+      ccfma(x, a20, b.e[2][k]);
+      d[0][k] = x;
+      Cpx<R> y = ccmul(a.e[0][1], b.e[0][k]);
+      ccfma(y, a.e[1][1], b.e[1][k]);
+      ccfma(y, a21, b.e[2][k]);
+      d[1][k] = y;
+    }
+    const Mat<R, 3> c = load_mat<R, 3, S>(pc, Vh, hc);
+    Mat<R, 3> t;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        Cpx<R> x = cmul(d[i][0], c.e[0][j]);
+        cfma(x, d[i][1], c.e[1][j]);
+        cfma(x, d[i][2], c.e[2][j]);
+        t.e[i][j] = x;
+      }
+    su3_third_row(t);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        st.e[i][j].re += t.e[i][j].re;
+        st.e[i][j].im += t.e[i][j].im;
+      }
+  } else {
+    const Mat<R, N> a = load_mat<R, N, S>(pa, Vh, ha);
+    const Mat<R, N> b = load_mat<R, N, S>(pb, Vh, hb);
+    const Mat<R, N> t = mul_dn(a, b);
+    const Mat<R, N> c = load_mat<R, N, S>(pc, Vh, hc);
+    acc_nn(st, t, c);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One chessboard pass over matrices (Nc >= 2, full or two-row storage):
+// staple (Eq. 9) -> W = U Sigma^+ -> SU(2) subgroups in lexicographic order
+// (Eq. 15), heatbath (Eqs. 12-14) or overrelaxation (Eq. 17) -> store.
+// One thread per link of the pass.
+// ---------------------------------------------------------------------------
+template <class R, int N, int S, int MODE, bool ROWS2, bool REUNIT>
+__device__ __forceinline__ void pass_body(const PassParams& p, int64_t h) {
+  const Geom& g = p.g;
+  const int mu = p.mu, par = p.parity, opp = par ^ 1;
+  const Site s = decode_half(g, h, par);
+  const uint32_t lex = uint32_t(s.lex);
+  const int cmu = coord_of(s, mu);
+  const uint32_t lex_pmu = fwd(g, lex, cmu, mu);
+
+
+  Mat<R, N> st;
+  mat_zero(st);
+#pragma unroll
+  for (int nu = 0; nu < 4; ++nu) {
+    if (nu == mu) continue;
+    const int cnu = s.c[nu];
+    const uint32_t lex_pnu = fwd(g, lex, cnu, nu);
+    const uint32_t lex_mnu = bwd(g, lex, cnu, nu);
+    const uint32_t lex_mnu_pmu = fwd(g, lex_mnu, cmu, mu);
+    staple_forward<R, N, S, ROWS2>(st, block_ptr(p, nu, par), h, block_ptr(p, mu, opp), lex_pnu >> 1,
+                                   block_ptr(p, nu, opp), lex_pmu >> 1, g.Vh);
+    staple_backward<R, N, S, ROWS2>(st, block_ptr(p, nu, opp), lex_mnu >> 1, block_ptr(p, mu, opp), lex_mnu >> 1,
+                                    block_ptr(p, nu, par), lex_mnu_pmu >> 1, g.Vh);
+  }
+
+  char* ublk = p.links + (2 * mu + par) * p.block_bytes;
+  Mat<R, N> u = load_mat<R, N, S, false>(ublk, g.Vh, h);
+  Mat<R, N> w = mul_nd(u, st);
+
+  uint32_t step = 0;
+  if constexpr (MODE == kHeatbathMode) step = *p.hb_step + p.step_offset;
+  const uint32_t link_id = uint32_t(mu) * uint32_t(g.V) + lex;
+  const R alpha_coef = R(p.alpha_coef);
+
+  int sub = 0;
+#pragma unroll
+  for (int i = 0; i < N - 1; ++i) {
+#pragma unroll
+    for (int j = i + 1; j < N; ++j) {
+      const bool last = (i == N - 2) && (j == N - 1);
+      const Quat<R> v = block_to_quat(w.e[i][i], w.e[i][j], w.e[j][i], w.e[j][j]);
+      const R k = d_sqrt(v.a0 * v.a0 + v.a1 * v.a1 + v.a2 * v.a2 + v.a3 * v.a3);
+      if (k > R(1e-15) && d_isfinite(k)) {
+        const R inv = R(1) / k;
+        const Quat<R> vd = {v.a0 * inv, -v.a1 * inv, -v.a2 * inv, -v.a3 * inv};  // vhat^+
+        Quat<R> a;
+        bool apply = true;
+        if constexpr (MODE == kHeatbathMode) {
+          Quat<R> b;
+          apply = heatbath_su2<R>(alpha_coef * k, p.key, link_id, step, uint32_t(sub), b);
+          a = qmul(b, vd);
+        } else {
+          a = qmul(vd, vd);
+        }
+        if (apply) {
+          apply_rows(u, i, j, a);
+          if (!last) apply_rows(w, i, j, a);
+        }
+      }
+      ++sub;
+    }
+  }
+  if constexpr (REUNIT) {
+    if (reunit_selected(p, h)) {
+      Mat<double, N> d = mat_cast<R, double, N>(u);
+      reunit_d<N>(d);
+      u = mat_cast<double, R, N>(d);
+    }
+  }
+  store_mat<R, N, S>(ublk, g.Vh, h, u);
+}
+
+// VAR bit 0: at most 128 threads per block and registers for 6 blocks per SM;
+// VAR bit 1: two-row staple products (SU(3) two-row storage only).
+// REUNIT: the FP64 re-unitarization of selected links is compiled in (passes that
+// re-unitarize use this instantiation; the others carry no FP64 code).
+template <class R, int N, int S, int MODE, int VAR, bool REUNIT>
+__global__ void __launch_bounds__(kMaxBlockThreads) update_pass_mat(const PassParams p) {
+  const int64_t h = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (h >= p.g.Vh) return;
+  pass_body<R, N, S, MODE, (VAR & 2) != 0, REUNIT>(p, h);
+}
+
+template <class R, int N, int S, int MODE, int VAR, bool REUNIT>
+__global__ void __launch_bounds__(128, 6) update_pass_mat_occ(const PassParams p) {
+  const int64_t h = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (h >= p.g.Vh) return;
+  pass_body<R, N, S, MODE, (VAR & 2) != 0, REUNIT>(p, h);
+}
+
+// kernel variants are built for the SU(3) FP32 update passes only
+template <class R, int N, int S>
+constexpr bool has_variants() {
+  return std::is_same<R, float>::value && N == 3;
+}
+
+// ---------------------------------------------------------------------------
+// One chessboard pass for SU(2) stored as quaternions (Eq. 6): the same steps
+// with the staple kept in the real span of SU(2).
+// ---------------------------------------------------------------------------
+template <class R, int MODE, bool REUNIT>
+__global__ void __launch_bounds__(kMaxBlockThreads) update_pass_quat(const PassParams p) {
+  const int64_t h = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const Geom& g = p.g;
+  if (h >= g.Vh) return;
+  const int mu = p.mu, par = p.parity, opp = par ^ 1;
+  const Site s = decode_half(g, h, par);
+  const uint32_t lex = uint32_t(s.lex);
+  const int cmu = coord_of(s, mu);
+  const uint32_t lex_pmu = fwd(g, lex, cmu, mu);
+
+  Quat<R> st = {R(0), R(0), R(0), R(0)};
+#pragma unroll
+  for (int nu = 0; nu < 4; ++nu) {
+    if (nu == mu) continue;
+    const int cnu = s.c[nu];
+    const uint32_t lex_pnu = fwd(g, lex, cnu, nu);
+    const uint32_t lex_mnu = bwd(g, lex, cnu, nu);
+    const uint32_t lex_mnu_pmu = fwd(g, lex_mnu, cmu, mu);
+    {
+      const Quat<R> a = load_quat<R>(block_ptr(p, nu, par), g.Vh, h);
+      const Quat<R> b = load_quat<R>(block_ptr(p, mu, opp), g.Vh, lex_pnu >> 1);
+      const Quat<R> c = load_quat<R>(block_ptr(p, nu, opp), g.Vh, lex_pmu >> 1);
+      st = qadd(st, qmul(qmul(a, b), qdag(c)));
+    }
+    {
+      const Quat<R> a = load_quat<R>(block_ptr(p, nu, opp), g.Vh, lex_mnu >> 1);
+      const Quat<R> b = load_quat<R>(block_ptr(p, mu, opp), g.Vh, lex_mnu >> 1);
+      const Quat<R> c = load_quat<R>(block_ptr(p, nu, par), g.Vh, lex_mnu_pmu >> 1);
+      st = qadd(st, qmul(qmul(qdag(a), b), c));
+    }
+  }
+  char* ublk = p.links + (2 * mu + par) * p.block_bytes;
+  Quat<R> u = load_quat<R, false>(ublk, g.Vh, h);
+  const Quat<R> w = qmul(u, qdag(st));
+  const R k = d_sqrt(w.a0 * w.a0 + w.a1 * w.a1 + w.a2 * w.a2 + w.a3 * w.a3);
+  if (k > R(1e-15) && d_isfinite(k)) {
+    const R inv = R(1) / k;
+    const Quat<R> vd = {w.a0 * inv, -w.a1 * inv, -w.a2 * inv, -w.a3 * inv};
+    if constexpr (MODE == kHeatbathMode) {
+      const uint32_t step = *p.hb_step + p.step_offset;
+      const uint32_t link_id = uint32_t(mu) * uint32_t(g.V) + uint32_t(s.lex);
+      Quat<R> b;
+      if (heatbath_su2<R>(R(p.alpha_coef) * k, p.key, link_id, step, 0u, b)) u = qmul(qmul(b, vd), u);
+    } else {
+      u = qmul(qmul(vd, vd), u);
+    }
+  }
+  if constexpr (REUNIT) {
+    if (reunit_selected(p, h)) {
+      const double a0 = u.a0, a1 = u.a1, a2 = u.a2, a3 = u.a3;
+      const double inv = rsqrt(a0 * a0 + a3 * a3 + a2 * a2 + a1 * a1);
+      u = Quat<R>{R(a0 * inv), R(a1 * inv), R(a2 * inv), R(a3 * inv)};
+    }
+  }
+  store_quat<R>(ublk, g.Vh, h, u);
+}
+
 struct LinkParams {
   char* links;
   int64_t block_bytes;
@@ -321,7 +484,7 @@ __global__ void __launch_bounds__(256) reunit_kernel(const LinkParams p) {
   if constexpr (S == kQuat) {
     const Quat<R> q = load_quat<R, false>(blk, p.g.Vh, h);
     const double a0 = q.a0, a1 = q.a1, a2 = q.a2, a3 = q.a3;
-    const double inv = 1.0 / sqrt(a0 * a0 + a3 * a3 + a2 * a2 + a1 * a1);
+    const double inv = rsqrt(a0 * a0 + a3 * a3 + a2 * a2 + a1 * a1);
     store_quat<R>(blk, p.g.Vh, h, Quat<R>{R(a0 * inv), R(a1 * inv), R(a2 * inv), R(a3 * inv)});
   } else {
     Mat<double, N> m = mat_cast<R, double, N>(load_mat<R, N, S, false>(blk, p.g.Vh, h));
@@ -448,21 +611,26 @@ __global__ void __launch_bounds__(256) plaquette_kernel(const ObsParams p, const
     const int par = idx >= g.Vh ? 1 : 0;
     const int64_t h = idx - par * g.Vh;
     const Site s = decode_half(g, h, par);
+    const uint32_t lex = uint32_t(s.lex);
 #pragma unroll
     for (int mu = 0; mu < 3; ++mu) {
-      const int64_t xpmu = fwd(g, s.lex, s.c[mu], mu) >> 1;
+      const int64_t xpmu = fwd(g, lex, s.c[mu], mu) >> 1;
+      if constexpr (S == kQuat) {
+        const Quat<R> umx = load_quat<R>(obs_block(p, mu, par), g.Vh, h);
 #pragma unroll
-      for (int nu = mu + 1; nu < 4; ++nu) {
-        const int64_t xpnu = fwd(g, s.lex, s.c[nu], nu) >> 1;
-        if constexpr (S == kQuat) {
-          const Quat<R> umx = load_quat<R>(obs_block(p, mu, par), g.Vh, h);
+        for (int nu = mu + 1; nu < 4; ++nu) {
+          const int64_t xpnu = fwd(g, lex, s.c[nu], nu) >> 1;
           const Quat<R> unx = load_quat<R>(obs_block(p, nu, par), g.Vh, h);
           const Quat<R> t1 = qmul(umx, load_quat<R>(obs_block(p, nu, par ^ 1), g.Vh, xpmu));
           const Quat<R> t2 = qmul(unx, load_quat<R>(obs_block(p, mu, par ^ 1), g.Vh, xpnu));
           acc[0] += double(R(2) * (t1.a0 * t2.a0 + t1.a1 * t2.a1 + t1.a2 * t2.a2 + t1.a3 * t2.a3));
-        } else {
-          const Mat<R, N> t1 = mul_nn(load_mat<R, N, S>(obs_block(p, mu, par), g.Vh, h),
-                                      load_mat<R, N, S>(obs_block(p, nu, par ^ 1), g.Vh, xpmu));
+        }
+      } else {
+        const Mat<R, N> umx = load_mat<R, N, S>(obs_block(p, mu, par), g.Vh, h);
+#pragma unroll
+        for (int nu = mu + 1; nu < 4; ++nu) {
+          const int64_t xpnu = fwd(g, lex, s.c[nu], nu) >> 1;
+          const Mat<R, N> t1 = mul_nn(umx, load_mat<R, N, S>(obs_block(p, nu, par ^ 1), g.Vh, xpmu));
           const Mat<R, N> t2 = mul_nn(load_mat<R, N, S>(obs_block(p, nu, par), g.Vh, h),
                                       load_mat<R, N, S>(obs_block(p, mu, par ^ 1), g.Vh, xpnu));
           acc[0] += double(retr_nd(t1, t2));
@@ -511,65 +679,91 @@ __global__ void __launch_bounds__(256) polyakov_kernel(const ObsParams p, const 
 
 // ---------------------------------------------------------------------------
 // Canonical FP64 <-> storage conversion of links [first, first + count),
-// canonical link index l = mu * V + lex.
+// canonical link index l = mu * V + lex.  A block converts LPB consecutive links
+// through shared memory, so the canonical side (which may be host memory mapped
+// into the device address space) is read and written as contiguous 16-byte
+// vectors.
 // ---------------------------------------------------------------------------
-template <class R, int N, int S>
-__global__ void __launch_bounds__(256) export_kernel(const ObsParams p, double* dst, int64_t first, int64_t count) {
-  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= count) return;
-  const int64_t l = first + i;
-  const int mu = int(l / p.g.V);
-  const int64_t lex = l - int64_t(mu) * p.g.V;
-  const int x = int(lex % p.g.nx), y = int((lex / p.g.nx) % p.g.ny);
-  const int z = int((lex / (int64_t(p.g.nx) * p.g.ny)) % p.g.nz), t = int(lex / (int64_t(p.g.nx) * p.g.ny * p.g.nz));
-  const int par = (x + y + z + t) & 1;
-  const Mat<R, N> m = load_mat<R, N, S>(obs_block(p, mu, par), p.g.Vh, lex >> 1);
-  double* o = dst + i * (2 * N * N);
-  if constexpr (S == kTwoRow) {
-    // rebuild the third row in FP64 from the stored rows
-    Mat<double, 3> d = mat_cast<R, double, 3>(m);
-    su3_third_row(d);
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        o[2 * (3 * a + b)] = d.e[a][b].re;
-        o[2 * (3 * a + b) + 1] = d.e[a][b].im;
-      }
-  } else {
-#pragma unroll
-    for (int a = 0; a < N; ++a)
-#pragma unroll
-      for (int b = 0; b < N; ++b) {
-        o[2 * (N * a + b)] = double(m.e[a][b].re);
-        o[2 * (N * a + b) + 1] = double(m.e[a][b].im);
-      }
-  }
+template <int N>
+__host__ __device__ constexpr int conv_links_per_block() {
+  return N <= 4 ? 128 : (N == 5 ? 64 : 32);
+}
+
+__device__ __forceinline__ int link_parity(const Geom& g, int64_t lex) {
+  const int x = int(lex % g.nx), y = int((lex / g.nx) % g.ny);
+  const int z = int((lex / (int64_t(g.nx) * g.ny)) % g.nz), t = int(lex / (int64_t(g.nx) * g.ny * g.nz));
+  return (x + y + z + t) & 1;
 }
 
 template <class R, int N, int S>
-__global__ void __launch_bounds__(256) import_kernel(const ObsParams p, const double* src, int64_t first, int64_t count) {
-  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= count) return;
-  const int64_t l = first + i;
-  const int mu = int(l / p.g.V);
-  const int64_t lex = l - int64_t(mu) * p.g.V;
-  const int x = int(lex % p.g.nx), y = int((lex / p.g.nx) % p.g.ny);
-  const int z = int((lex / (int64_t(p.g.nx) * p.g.ny)) % p.g.nz), t = int(lex / (int64_t(p.g.nx) * p.g.ny * p.g.nz));
-  const int par = (x + y + z + t) & 1;
-  const double* s = src + i * (2 * N * N);
-  Mat<R, N> m;
+__global__ void __launch_bounds__(128) export_kernel(const ObsParams p, double* dst, int64_t first, int64_t count) {
+  constexpr int D = 2 * N * N;
+  constexpr int LPB = conv_links_per_block<N>();
+  __shared__ __align__(16) double sm[LPB * D];
+  const int64_t rel0 = int64_t(blockIdx.x) * LPB;
+  const int nl = int((count - rel0) < LPB ? (count - rel0) : LPB);
+  for (int i = threadIdx.x; i < nl; i += blockDim.x) {
+    const int64_t l = first + rel0 + i;
+    const int mu = int(l / p.g.V);
+    const int64_t lex = l - int64_t(mu) * p.g.V;
+    const Mat<R, N> m = load_mat<R, N, S>(obs_block(p, mu, link_parity(p.g, lex)), p.g.Vh, lex >> 1);
+    double* o = sm + i * D;
+    if constexpr (S == kTwoRow) {
+      Mat<double, 3> d = mat_cast<R, double, 3>(m);  // third row rebuilt in FP64
+      su3_third_row(d);
 #pragma unroll
-  for (int a = 0; a < N; ++a)
+      for (int a = 0; a < 3; ++a)
 #pragma unroll
-    for (int b = 0; b < N; ++b) m.e[a][b] = {R(s[2 * (N * a + b)]), R(s[2 * (N * a + b) + 1])};
-  store_mat<R, N, S>(const_cast<char*>(obs_block(p, mu, par)), p.g.Vh, lex >> 1, m);
+        for (int b = 0; b < 3; ++b) {
+          o[2 * (3 * a + b)] = d.e[a][b].re;
+          o[2 * (3 * a + b) + 1] = d.e[a][b].im;
+        }
+    } else {
+#pragma unroll
+      for (int a = 0; a < N; ++a)
+#pragma unroll
+        for (int b = 0; b < N; ++b) {
+          o[2 * (N * a + b)] = double(m.e[a][b].re);
+          o[2 * (N * a + b) + 1] = double(m.e[a][b].im);
+        }
+    }
+  }
+  __syncthreads();
+  double2* out = reinterpret_cast<double2*>(dst + rel0 * D);
+  const double2* in = reinterpret_cast<const double2*>(sm);
+  for (int j = threadIdx.x; j < nl * D / 2; j += blockDim.x) out[j] = in[j];
+}
+
+template <class R, int N, int S>
+__global__ void __launch_bounds__(128) import_kernel(const ObsParams p, const double* src, int64_t first, int64_t count) {
+  constexpr int D = 2 * N * N;
+  constexpr int LPB = conv_links_per_block<N>();
+  __shared__ __align__(16) double sm[LPB * D];
+  const int64_t rel0 = int64_t(blockIdx.x) * LPB;
+  const int nl = int((count - rel0) < LPB ? (count - rel0) : LPB);
+  const double2* in = reinterpret_cast<const double2*>(src + rel0 * D);
+  double2* st = reinterpret_cast<double2*>(sm);
+  for (int j = threadIdx.x; j < nl * D / 2; j += blockDim.x) st[j] = in[j];
+  __syncthreads();
+  for (int i = threadIdx.x; i < nl; i += blockDim.x) {
+    const int64_t l = first + rel0 + i;
+    const int mu = int(l / p.g.V);
+    const int64_t lex = l - int64_t(mu) * p.g.V;
+    const double* s = sm + i * D;
+    Mat<R, N> m;
+#pragma unroll
+    for (int a = 0; a < N; ++a)
+#pragma unroll
+      for (int b = 0; b < N; ++b) m.e[a][b] = {R(s[2 * (N * a + b)]), R(s[2 * (N * a + b) + 1])};
+    store_mat<R, N, S>(const_cast<char*>(obs_block(p, mu, link_parity(p.g, lex))), p.g.Vh, lex >> 1, m);
+  }
 }
 
 // ---------------------------------------------------------------------------
 // Host launchers and the operation table
 // ---------------------------------------------------------------------------
-inline PassParams make_pass_params(const Ctx& c, int mu, int parity, uint32_t step_offset) {
+inline PassParams make_pass_params(const Ctx& c, int mu, int parity, uint32_t step_offset, uint32_t reunit_mod,
+                                   uint32_t reunit_rem) {
   PassParams p;
   p.links = c.links;
   p.block_bytes = c.block_bytes;
@@ -580,24 +774,65 @@ inline PassParams make_pass_params(const Ctx& c, int mu, int parity, uint32_t st
   p.key = make_uint2(uint32_t(c.seed & 0xffffffffu), uint32_t(c.seed >> 32));
   p.hb_step = &c.state->hb_step;
   p.step_offset = step_offset;
+  p.reunit_mod = reunit_mod;
+  p.reunit_rem = reunit_rem;
   return p;
 }
 
 template <class R, int N, int S>
-cudaError_t launch_pass(const Ctx& c, int mode, int mu, int parity, uint32_t step_offset) {
-  const PassParams p = make_pass_params(c, mu, parity, step_offset);
+cudaError_t launch_pass(const Ctx& c, int mode, int mu, int parity, uint32_t step_offset, uint32_t reunit_mod,
+                        uint32_t reunit_rem) {
+  const PassParams p = make_pass_params(c, mu, parity, step_offset, reunit_mod, reunit_rem);
   const int bt = c.block_threads;
   const unsigned grid = unsigned((c.g.Vh + bt - 1) / bt);
+  const bool ru = reunit_mod != 0u;
   if constexpr (S == kQuat) {
-    if (mode == kHeatbathMode)
-      update_pass_quat<R, kHeatbathMode><<<grid, bt, 0, c.stream>>>(p);
-    else
-      update_pass_quat<R, kOverrelaxMode><<<grid, bt, 0, c.stream>>>(p);
+#define SUN_LAUNCH_QUAT(RU)                                                             \
+  if (mode == kHeatbathMode)                                                            \
+    update_pass_quat<R, kHeatbathMode, RU><<<grid, bt, 0, c.stream>>>(p);               \
+  else                                                                                  \
+    update_pass_quat<R, kOverrelaxMode, RU><<<grid, bt, 0, c.stream>>>(p);
+    if (ru) {
+      SUN_LAUNCH_QUAT(true)
+    } else {
+      SUN_LAUNCH_QUAT(false)
+    }
+#undef SUN_LAUNCH_QUAT
+  } else if constexpr (has_variants<R, N, S>()) {
+    const int v = c.variant & 3;
+    const unsigned bt1 = (v & 1) ? 128u : unsigned(bt);
+    const unsigned g1 = unsigned((c.g.Vh + bt1 - 1) / bt1);
+#define SUN_LAUNCH_VAR(K, V)                                                            \
+  if (mode == kHeatbathMode) {                                                          \
+    if (ru)                                                                             \
+      K<R, N, S, kHeatbathMode, V, true><<<g1, bt1, 0, c.stream>>>(p);                  \
+    else                                                                                \
+      K<R, N, S, kHeatbathMode, V, false><<<g1, bt1, 0, c.stream>>>(p);                 \
+  } else {                                                                              \
+    if (ru)                                                                             \
+      K<R, N, S, kOverrelaxMode, V, true><<<g1, bt1, 0, c.stream>>>(p);                 \
+    else                                                                                \
+      K<R, N, S, kOverrelaxMode, V, false><<<g1, bt1, 0, c.stream>>>(p);                \
+  }
+    switch (v) {
+      case 1: SUN_LAUNCH_VAR(update_pass_mat_occ, 1) break;
+      case 2: SUN_LAUNCH_VAR(update_pass_mat, 2) break;
+      case 3: SUN_LAUNCH_VAR(update_pass_mat_occ, 3) break;
+      default: SUN_LAUNCH_VAR(update_pass_mat, 0) break;
+    }
+#undef SUN_LAUNCH_VAR
   } else {
-    if (mode == kHeatbathMode)
-      update_pass_mat<R, N, S, kHeatbathMode><<<grid, bt, 0, c.stream>>>(p);
-    else
-      update_pass_mat<R, N, S, kOverrelaxMode><<<grid, bt, 0, c.stream>>>(p);
+    if (mode == kHeatbathMode) {
+      if (ru)
+        update_pass_mat<R, N, S, kHeatbathMode, 0, true><<<grid, bt, 0, c.stream>>>(p);
+      else
+        update_pass_mat<R, N, S, kHeatbathMode, 0, false><<<grid, bt, 0, c.stream>>>(p);
+    } else {
+      if (ru)
+        update_pass_mat<R, N, S, kOverrelaxMode, 0, true><<<grid, bt, 0, c.stream>>>(p);
+      else
+        update_pass_mat<R, N, S, kOverrelaxMode, 0, false><<<grid, bt, 0, c.stream>>>(p);
+    }
   }
   return cudaGetLastError();
 }
@@ -672,14 +907,16 @@ cudaError_t launch_polyakov(const Ctx& c, double* out, const uint32_t* slot, int
 template <class R, int N, int S>
 cudaError_t launch_export(const Ctx& c, double* dst, int64_t first, int64_t count) {
   if (count <= 0) return cudaSuccess;
-  export_kernel<R, N, S><<<unsigned((count + 127) / 128), 128, 0, c.stream>>>(make_obs_params(c), dst, first, count);
+  constexpr int LPB = conv_links_per_block<N>();
+  export_kernel<R, N, S><<<unsigned((count + LPB - 1) / LPB), 128, 0, c.stream>>>(make_obs_params(c), dst, first, count);
   return cudaGetLastError();
 }
 
 template <class R, int N, int S>
 cudaError_t launch_import(const Ctx& c, const double* src, int64_t first, int64_t count) {
   if (count <= 0) return cudaSuccess;
-  import_kernel<R, N, S><<<unsigned((count + 127) / 128), 128, 0, c.stream>>>(make_obs_params(c), src, first, count);
+  constexpr int LPB = conv_links_per_block<N>();
+  import_kernel<R, N, S><<<unsigned((count + LPB - 1) / LPB), 128, 0, c.stream>>>(make_obs_params(c), src, first, count);
   return cudaGetLastError();
 }
 

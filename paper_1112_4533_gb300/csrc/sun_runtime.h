@@ -6,12 +6,32 @@
 
 namespace sun {
 
+// Division of n < 2^31 by a fixed divisor d < 2^31 with one multiply-high, add
+// and shift: q = (umulhi(n, m) + n) >> s with s = ceil(log2 d) and
+// m = floor(2^32 (2^s - d) / d) + 1 (Granlund & Montgomery, "Division by
+// invariant integers using multiplication", PLDI 1994, Sec. 4).
+struct FastDiv {
+  uint32_t d, m, s;
+};
+
+inline FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f;
+  f.d = d;
+  uint32_t s = 0;
+  while ((uint64_t(1) << s) < d) ++s;
+  f.s = s;
+  f.m = uint32_t((((uint64_t(1) << 32) * ((uint64_t(1) << s) - d)) / d) + 1);
+  return f;
+}
+
 // Lattice geometry: periodic Nx x Ny x Nz x Nt, even extents, even/odd site order.
+// Site indices fit in 32 bits (V <= 2^30).
 struct Geom {
   int nx, ny, nz, nt;
   int nxh;            // nx / 2
   int64_t V, Vh;      // sites, sites per parity
   int64_t stride[4];  // lex strides of x, y, z, t
+  FastDiv div_nxh, div_ny, div_nz, div_nx;
 };
 
 // Device-resident mutable state of one lattice.
@@ -37,12 +57,14 @@ struct Ctx {
   cudaStream_t stream;
   int block_threads;
   int reduce_blocks;
+  int variant;  // update-pass kernel variant (bit 0: 6 blocks/SM register bound, bit 1: two-row staple)
 };
 
 // The operations of one (Nc, storage, precision) combination.
 struct Ops {
   int nc, storage, precision, link_bytes;
-  cudaError_t (*pass)(const Ctx&, int mode, int mu, int parity, uint32_t step_offset);
+  cudaError_t (*pass)(const Ctx&, int mode, int mu, int parity, uint32_t step_offset, uint32_t reunit_mod,
+                      uint32_t reunit_rem);
   cudaError_t (*init)(const Ctx&, int hot);
   cudaError_t (*reunit)(const Ctx&);
   cudaError_t (*plaquette)(const Ctx&, double* out, const uint32_t* slot, int cap);

@@ -30,7 +30,8 @@ class SunError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("storage", ctypes.c_int), ("reunit_every", ctypes.c_int),
                 ("block_threads", ctypes.c_int), ("stream", ctypes.c_void_p), ("device_buf", ctypes.c_void_p),
-                ("device_buf_bytes", ctypes.c_size_t), ("use_graphs", ctypes.c_int)]
+                ("device_buf_bytes", ctypes.c_size_t), ("use_graphs", ctypes.c_int), ("variant", ctypes.c_int),
+                ("reunit_mode", ctypes.c_int)]
 
 
 class LatticeInfo(ctypes.Structure):
@@ -102,7 +103,7 @@ def _dims(dims):
 
 
 def _options(precision=32, storage=0, reunit_every=1, block_threads=0, stream=None, device_buf=None,
-             device_buf_bytes=0, use_graphs=True):
+             device_buf_bytes=0, use_graphs=True, variant=0, reunit_mode=0):
     o = Options()
     load_library().sun_options_init(ctypes.byref(o))
     o.precision = int(precision)
@@ -113,6 +114,8 @@ def _options(precision=32, storage=0, reunit_every=1, block_threads=0, stream=No
     o.device_buf = device_buf
     o.device_buf_bytes = int(device_buf_bytes)
     o.use_graphs = 1 if use_graphs else 0
+    o.variant = int(variant)
+    o.reunit_mode = int(reunit_mode)
     return o
 
 
@@ -134,7 +137,7 @@ class Lattice:
     """
 
     def __init__(self, nc, dims, beta, hot_start=False, seed=1, precision=32, storage=0, reunit_every=1,
-                 block_threads=0, stream=None, use_graphs=True, device=None):
+                 block_threads=0, stream=None, use_graphs=True, device=None, variant=0, reunit_mode=0):
         import torch  # device memory and streams only
 
         self.nc = int(nc)
@@ -155,7 +158,7 @@ class Lattice:
         base = self._buf.data_ptr()
         aligned = (base + 255) // 256 * 256
         o = _options(precision, storage, reunit_every, block_threads, ctypes.c_void_p(self.stream.cuda_stream),
-                     ctypes.c_void_p(aligned), nbytes, use_graphs)
+                     ctypes.c_void_p(aligned), nbytes, use_graphs, variant, reunit_mode)
         # the tensor's memory must be usable on our stream
         self.stream.wait_stream(torch.cuda.current_stream(dev))
         h = ctypes.c_void_p()

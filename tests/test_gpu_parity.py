@@ -100,11 +100,14 @@ def test_import_export_roundtrip(sunlib, cfg):
 PASS_DIMS = (8, 6, 4, 10)  # V/2 = 960: several 128-thread blocks and a ragged tail
 
 
-@pytest.mark.parametrize("cfg", CONFIGS)
+VARIANT_CASES = [c + (0,) for c in CONFIGS] + [(3, st, 32, v) for st in (12, 18) for v in (1, 2, 3)]
+
+
+@pytest.mark.parametrize("cfg", VARIANT_CASES)
 def test_overrelaxation_pass_matches_oracle(sunlib, cfg):
-    nc, st, prec = cfg
+    nc, st, prec, variant = cfg
     U0 = thermal_config(nc, PASS_DIMS, seed=10 + nc)
-    with gpu_lattice(sunlib, nc, PASS_DIMS, st, prec, U0) as L:
+    with gpu_lattice(sunlib, nc, PASS_DIMS, st, prec, U0, variant=variant) as L:
         start = L.export_links()  # the stored (rounded / two-row) representation
         for mu, par in [(0, 0), (3, 1), (1, 1), (2, 0)]:
             before = L.export_links()
@@ -117,13 +120,13 @@ def test_overrelaxation_pass_matches_oracle(sunlib, cfg):
         assert maxdiff(start, got) > 1e-3
 
 
-@pytest.mark.parametrize("cfg", CONFIGS)
+@pytest.mark.parametrize("cfg", VARIANT_CASES)
 def test_heatbath_pass_matches_oracle(sunlib, cfg):
-    nc, st, prec = cfg
+    nc, st, prec, variant = cfg
     U0 = thermal_config(nc, PASS_DIMS, seed=20 + nc)
     n_updates = 0
     flips = 0
-    with gpu_lattice(sunlib, nc, PASS_DIMS, st, prec, U0, seed=31) as L:
+    with gpu_lattice(sunlib, nc, PASS_DIMS, st, prec, U0, seed=31, variant=variant) as L:
         L.heatbath_step = 5
         for mu, par in [(1, 0), (2, 1), (0, 1), (3, 0)]:
             before = L.export_links()
@@ -208,29 +211,70 @@ def test_su2_small_workload_history_matches_oracle(sunlib):
 
 @pytest.mark.parametrize("nc,st", [(2, 4), (3, 18), (4, 32), (6, 72)])
 def test_fp64_sweeps_follow_the_oracle(sunlib, nc, st):
-    """Three FP64 sweeps, each compared from the same input."""
+    """Three FP64 sweeps (1 heatbath + 2 overrelaxation + reunitarization)
+    from a Haar start, every pass compared with the oracle from the same input
+    (1e-12).  Whole sweeps are not compared: within one sweep the chain
+    amplifies rounding-order differences to 1e-11 (SU(3)) .. 1e-7 (SU(6))."""
     dims = (4, 6, 4, 4)
     beta = beta_for(nc)
     with sunlib.Lattice(nc, dims, beta, hot_start=True, seed=17, precision=64, storage=st) as L:
         for s in range(3):
-            start = L.export_links()
-            L.sweep(1, 2)
+            L.heatbath_step = s
+            for mode in (orc.HEATBATH, orc.OVERRELAX, orc.OVERRELAX):
+                for mu in range(4):
+                    for par in range(2):
+                        before = L.export_links()
+                        L.update_pass(mode, mu, par)
+                        got = L.export_links()
+                        orc.update_pass(before, beta, mode, mu, par, s, 17)
+                        assert maxdiff(got, before) < 1e-12, (s, mode, mu, par)
+            before = L.export_links()
+            L.reunitarize()
             got = L.export_links()
-            want = start.copy()
-            orc.sweep(want, beta, 1, 2, True, 17, s)
-            assert maxdiff(got, want) < 1e-11, s
+            orc.reunitarize(before)
+            assert maxdiff(got, before) < 1e-13
 
 
-def test_su3_medium_workload_sweep_pass_by_pass(sunlib):
+def subgroup_strength(U, mu, par):
+    """Per link of the pass (mu, par): the smallest projected SU(2) strength k of
+    W = U Sigma^+ over the subgroups, from the oracle's staple.  FP32 rounding of
+    the staple enters the update divided by k, so it sets each link's tolerance."""
+    nc = U.shape[-1]
+    nx, ny, nz, nt = U.shape[4], U.shape[3], U.shape[2], U.shape[1]
+    flat = U.reshape(4, -1, nc, nc)
+    kmin = np.full(flat.shape[1], np.inf)
+    for lex in range(flat.shape[1]):
+        x, y, z, t = lex % nx, (lex // nx) % ny, (lex // (nx * ny)) % nz, lex // (nx * ny * nz)
+        if (x + y + z + t) % 2 != par:
+            continue
+        w = flat[mu, lex] @ np.conj(orc.staple(U, mu, lex)).T
+        for i in range(nc - 1):
+            for j in range(i + 1, nc):
+                b = w[np.ix_([i, j], [i, j])]
+                q = 0.5 * np.array([(b[0, 0] + b[1, 1]).real, (b[0, 1] + b[1, 0]).imag,
+                                    (b[0, 1] - b[1, 0]).real, (b[0, 0] - b[1, 1]).imag])
+                kmin[lex] = min(kmin[lex], np.linalg.norm(q))
+    return kmin
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_su3_medium_workload_sweep_pass_by_pass(sunlib, variant):
     """SU(3) 16^4, beta 6.0, Haar start, FP32 12-real: every pass of one sweep
     (1 heatbath + 4 overrelaxation steps, 40 passes) and the FP64
-    reunitarization, each compared with the oracle from the same input."""
+    reunitarization, each compared with the oracle from the same input.
+    Overrelaxation links agree to 1e-5 where every subgroup strength k >= 1
+    and to 1e-5 / k below (a Haar start has some nearly cancelling staples).
+    Variants with bit 2 (staple terms' third row taken as conj(row0 x row1))
+    assume unitary links; before the sweep's re-unitarization the links of a
+    Haar start drift by ~1e-6 and those variants are held to 2e-5."""
+    bound = 2e-5 if variant & 2 else 1e-5
     dims = (16, 16, 16, 16)
     n_updates, flips = 0, 0
-    with sunlib.Lattice(3, dims, 6.0, hot_start=True, seed=2, precision=32, storage=12) as L:
+    worst = 0.0
+    with sunlib.Lattice(3, dims, 6.0, hot_start=True, seed=2, precision=32, storage=12, variant=variant) as L:
         hot = L.export_links()
         assert maxdiff(hot, orc.init(3, dims, True, 2)) < 5e-7
-        for mode in [orc.HEATBATH] + [orc.OVERRELAX] * 4:
+        for step, mode in enumerate([orc.HEATBATH] + [orc.OVERRELAX] * 4):
             for mu in range(4):
                 for par in range(2):
                     before = L.export_links()
@@ -242,8 +286,15 @@ def test_su3_medium_workload_sweep_pass_by_pass(sunlib):
                     if mode == orc.HEATBATH:
                         flips += int((d > 1e-5).sum())
                         n_updates += d.size // 2
+                    elif d.max() >= 1e-5:
+                        k = subgroup_strength(before, mu, par)
+                        scaled = (d * np.minimum(1.0, k))[np.isfinite(k)]
+                        print(f"variant {variant} step {step} mu {mu} par {par}: max {d.max():.3e} "
+                              f"scaled {scaled.max():.3e} at k={k[np.argmax(d)]:.3f}")
+                        assert scaled.max() < bound, (step, mu, par, d.max(), scaled.max())
+                        worst = max(worst, d.max())
                     else:
-                        assert d.max() < 1e-5, (mu, par, d.max())
+                        worst = max(worst, d.max())
         before = L.export_links()
         L.reunitarize()
         got = L.export_links()
@@ -277,6 +328,31 @@ def test_equilibrium_plaquette_agrees_with_oracle(sunlib, nc, beta, st, prec):
     mg, eg = mean_err(g)
     mo, eo = mean_err(o)
     assert abs(mg - mo) < 3 * np.hypot(eg, eo), (mg, eg, mo, eo)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("cfg", [(2, 4, 64), (3, 18, 64), (3, 12, 64), (4, 32, 64), (2, 4, 32), (3, 12, 32)])
+def test_fused_reunitarization_sweep_matches_oracle(sunlib, cfg, mode):
+    """reunit_mode 1 (each link of the last step re-unitarized in the update
+    kernel) and 2 (runs of 32 links spread over the steps) against the oracle's
+    schedules, one sweep from a thermal configuration; the result is special
+    unitary to the storage precision."""
+    nc, st, prec = cfg
+    dims = (8, 6, 4, 4)  # 96 sites per parity: three runs of 32
+    U0 = thermal_config(nc, dims, seed=90 + nc)
+    with gpu_lattice(sunlib, nc, dims, st, prec, U0, seed=6, reunit_mode=mode) as L:
+        start = L.export_links()
+        L.sweep(1, 1)
+        got = L.export_links()
+    want = start.copy()
+    orc.sweep(want, beta_for(nc), 1, 1, orc.REUNIT_FUSED if mode == 1 else orc.REUNIT_SPREAD, 6, 0)
+    d = np.abs(got - want).reshape(-1, nc * nc).max(axis=1)
+    if prec == 64:
+        assert d.max() < 1e-10
+    else:
+        assert np.median(d) < 1e-6 and (d > 1e-4).mean() < 1e-3
+    m = got.reshape(-1, nc, nc)
+    assert np.abs(m @ np.conj(np.swapaxes(m, 1, 2)) - np.eye(nc)).max() < (1e-14 if prec == 64 else 2e-6)
 
 
 # ------------------------------------------------------- equivalences ----
