@@ -182,6 +182,32 @@ typedef struct {
 } sun_lattice_info;
 sun_status sun_get_info(const sun_lattice* lat, sun_lattice_info* info);
 
+/* Plaquette of link storage the caller already holds, with no allocation.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory when they measure -- code confined to a memory
+ * arena it does not own, code enqueuing work while a stream is captured into a
+ * CUDA graph, latency-critical loops that cannot afford an allocation's
+ * implicit synchronisation.
+ *  links      device address of link storage in this library's layout (e.g.
+ *             sun_lattice_info.links of a lattice with the same nc, dims,
+ *             precision, storage); read only
+ *  nc, dims, precision, storage  as for sun_lattice_create (storage 0 = default)
+ *  out        device address of one double that receives <P> (Eq. 4 normalised
+ *             as sun_plaquette); the caller owns it
+ *  stream     cudaStream_t to enqueue on (NULL = the legacy default stream); the
+ *             call is asynchronous and does not synchronise
+ * Calls no cudaMalloc, cudaFree or allocating library routine.  The reduction
+ * scratch is a fixed array in the library's device image: 512 KiB + 256 B on every
+ * GPU that loads the library, held until the process exits, so at most
+ * 16,777,216 sites (65,536 blocks of 256 sites) -- larger lattices are rejected
+ * with SUN_ERR_ARG.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress, with that device current): make that first call
+ * before any stream capture.  Every call shares the array and re-arms its
+ * counter: calls that overlap on the GPU (other streams, other host threads
+ * without ordering) race -- order them on one stream. */
+sun_status sun_plaquette_noalloc(const void* links, int nc, const int dims[4], int precision,
+                                 int storage, double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

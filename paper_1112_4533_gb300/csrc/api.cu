@@ -122,6 +122,10 @@ struct GraphKey {
 
 }  // namespace
 
+namespace sun {
+void set_last_error_message(const char* msg) { g_last_error = msg ? msg : ""; }
+}  // namespace sun
+
 struct sun_lattice {
   int nc = 0, precision = 0, storage = 0;
   int dims[4] = {0, 0, 0, 0};

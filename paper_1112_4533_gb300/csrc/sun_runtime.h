@@ -79,4 +79,7 @@ const Ops* ops_su4(int storage, int precision);
 const Ops* ops_su5(int storage, int precision);
 const Ops* ops_su6(int storage, int precision);
 
+// sets the calling thread's sun_last_error() message
+void set_last_error_message(const char* msg);
+
 }  // namespace sun

@@ -69,6 +69,7 @@ SIGNATURES = [
     ("sun_set_beta", ctypes.c_int, [_P, ctypes.c_double]),
     ("sun_synchronize", ctypes.c_int, [_P]),
     ("sun_get_info", ctypes.c_int, [_P, ctypes.POINTER(LatticeInfo)]),
+    ("sun_plaquette_noalloc", ctypes.c_int, [_P, ctypes.c_int, _I4, ctypes.c_int, ctypes.c_int, _D, _P]),
 ]
 
 
