@@ -20,6 +20,15 @@ hot path).
 
 --impl reference times the CPU oracle alone on the same workload and metric.
 Multi-GPU: independent replicas (one lattice per rank), weak scaling.
+
+--workload batched: 64 independent SU(3) chains, L drawn from {8,12,16,24},
+beta uniform in [5.6, 6.4], Haar start, 50 sweeps (1 heatbath + 4
+overrelaxation) of every chain per step, all chains in one batch (a captured
+CUDA graph per batch sweep), against the same chains run one at a time.
+--workload serving: a Poisson request trace (mean 20/s) of SU(Nc) chains,
+Nc in {2,3,4,6}, L in {8..24}, 20..200 sweeps each, served by continuous
+batching under a device-memory budget, against the same trace served one
+request at a time; p50/p99 latency and throughput.
 """
 import argparse
 import hashlib
@@ -387,6 +396,91 @@ def gpu_arm(args):
         dist.destroy_process_group()
 
 
+def batched_arm(args):
+    import numpy as np
+    import torch
+    import paper_1112_4533_gb300 as sun
+
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(4)
+    n = 64
+    Ls = rng.choice([8, 12, 16, 24], size=n)
+    betas = rng.uniform(5.6, 6.4, size=n)
+    sweeps = 50
+    kw = dict(precision=32, storage=args.storage, reunit_mode=args.reunit_mode, variant=args.variant)
+    lats = [sun.Lattice(3, (int(L),) * 4, float(b), hot_start=True, seed=100 + i, **kw)
+            for i, (L, b) in enumerate(zip(Ls, betas))]
+    updates = sum((1 + 4) * 4 * int(L) ** 4 for L in Ls) * sweeps
+    B = sun.Batch(lats, use_graphs=True)
+    B.run(max(1, args.warmup), 1, 4)
+    torch.cuda.synchronize()
+    t = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        B.run(sweeps, 1, 4)
+        t.append(time.perf_counter() - t0)
+    B.close()
+    # plain path: the same chains, one at a time
+    for L in lats:
+        L.run(1, 1, 4)
+    torch.cuda.synchronize()
+    tp = []
+    for _ in range(max(1, args.steps // 2)):
+        t0 = time.perf_counter()
+        for L in lats:
+            L.run(sweeps, 1, 4)
+        torch.cuda.synchronize()
+        tp.append(time.perf_counter() - t0)
+    for L in lats:
+        L.close()
+    tb, tpl = min(t), min(tp)
+    out = {"metric": "batched chains/s", "value": n / tb, "unit": "chains/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": tb * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic (Haar starts, seeds 100..163)",
+           "config": {"workload": "64 SU(3) chains, L in {8,12,16,24} (seeded draw), beta U[5.6,6.4], hot start, "
+                                  "50 sweeps of 1 heatbath + 4 overrelaxation each, FP32 two-row",
+                      "L_counts": {str(v): int((Ls == v).sum()) for v in (8, 12, 16, 24)},
+                      "link_updates_per_step": updates, "storage_reals": args.storage, "kernel_variant": args.variant,
+                      "reunit_mode": args.reunit_mode},
+           "link_updates_per_s": updates / tb,
+           "plain": {"value": n / tpl, "unit": "chains/s", "ms_per_step": tpl * 1e3, "link_updates_per_s": updates / tpl,
+                     "path": "each chain alone, sun_run of 50 sweeps (one captured sweep graph per chain)"},
+           "speedup_vs_plain": tpl / tb}
+    print(json.dumps(out))
+
+
+def serving_arm(args):
+    import torch
+    from paper_1112_4533_gb300 import serve
+
+    torch.cuda.set_device(0)
+    trace = serve.poisson_trace(args.requests, rate=20.0, seed=7)
+    budget = int(args.budget_gb * (1 << 30))
+    warm = serve.poisson_trace(4, rate=50.0, seed=99, Ls=(8,), sweeps=(2, 3))
+    serve.Server(budget).run(warm)  # load kernels
+    srv = serve.Server(budget, sweeps_per_tick=args.sweeps_per_tick)
+    t0 = time.perf_counter()
+    out = srv.run(trace)
+    wall = time.perf_counter() - t0
+    st = serve.latency_stats(out)
+    plain, pwall, pupd = serve.serve_plain(trace)
+    pst = serve.latency_stats(plain)
+    upd = sum(r.n_sweeps * 5 * 4 * r.L ** 4 for r in trace)
+    res = {"metric": "p50 request latency", "value": st["p50_s"], "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 1,
+           "ms_per_step": wall * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32", "data": "synthetic Poisson trace (seed 7)",
+           "config": {"workload": f"{args.requests} requests, Poisson mean 20/s, Nc in {{2,3,4,6}}, L in "
+                                  "{8,12,16,20,24}, 20..200 sweeps of 1 heatbath + 4 overrelaxation, FP32",
+                      "hbm_budget_gb": args.budget_gb, "sweeps_per_tick": args.sweeps_per_tick},
+           "p99_s": st["p99_s"], "mean_s": st["mean_s"], "completed": st["completed"],
+           "throughput": {"requests_per_s": len(trace) / wall, "link_updates_per_s": upd / wall},
+           "plain": {"p50_s": pst["p50_s"], "p99_s": pst["p99_s"], "mean_s": pst["mean_s"],
+                     "requests_per_s": len(trace) / pwall, "link_updates_per_s": pupd / pwall,
+                     "path": "one request at a time in arrival order, sun_run per chain"},
+           "ticks": srv.ticks}
+    print(json.dumps(res))
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -427,11 +521,19 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--workload", choices=["single", "batched", "serving"], default="single")
+    ap.add_argument("--requests", type=int, default=80)
+    ap.add_argument("--budget-gb", type=float, default=64.0)
+    ap.add_argument("--sweeps-per-tick", type=int, default=2)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         reference_arm(args)
+    elif args.workload == "batched":
+        batched_arm(args)
+    elif args.workload == "serving":
+        serving_arm(args)
     else:
         gpu_arm(args)
 

@@ -88,6 +88,7 @@ enum { SUN_HEATBATH = 0, SUN_OVERRELAX = 1 };
  *                steps: links in runs of 32 consecutive even/odd site indices
  *                (lex >> 1), run r re-unitarized right after its update in step
  *                r mod (n_heatbath + n_overrelax), inside the update kernel.
+ *                Modes 1 and 2 are not built for FP64 with Nc >= 5 (SUN_ERR_UNSUPPORTED).
  */
 typedef struct {
   int precision;
@@ -181,6 +182,36 @@ typedef struct {
   void* stream;          /* cudaStream_t the lattice enqueues on         */
 } sun_lattice_info;
 sun_status sun_get_info(const sun_lattice* lat, sun_lattice_info* info);
+
+/* ---------------------------------------------------------------------------
+ * Batches: many independent chains swept together.
+ * A batch references existing lattices (they must outlive it) of possibly
+ * different Nc, extents, beta and seed.  Lattices with the same (Nc, storage,
+ * precision) form a group; each chessboard pass, re-unitarization and
+ * observable of a group is one kernel launch over all its chains (block ->
+ * chain table), and groups run on their own streams so that their kernels
+ * overlap.  Each chain evolves exactly as it would alone: same kernels per link,
+ * its own seed and heatbath step counter, and per-chain FP64 observable sums
+ * in a fixed order.  All lattices must share reunit_every (0 or 1) and
+ * reunit_mode; a batch uses the kernel variant and block size of each group's
+ * first lattice.
+ */
+typedef struct sun_batch sun_batch;
+
+/* stream: cudaStream_t the batch synchronises with (NULL = one the batch creates);
+ * use_graphs: sun_batch_run captures one batch sweep as a CUDA graph and replays it. */
+sun_status sun_batch_create(sun_batch** out, sun_lattice* const* lattices, int n, void* stream,
+                            int use_graphs);
+
+/* n_sweeps sweeps of every chain as sun_run (n_heatbath heatbath + n_overrelax
+ * overrelaxation steps, re-unitarization per the lattices' options), each followed
+ * by the plaquette (plaq: n_sweeps x n doubles, row = sweep, column = the chain's
+ * position in the create call) and the Polyakov loop (poly: n_sweeps x n x 2)
+ * when the pointers are not NULL.  Each chain's heatbath counter advances by
+ * n_sweeps * n_heatbath.  Waits for the lattices' own streams first.  Syncs. */
+sun_status sun_batch_run(sun_batch* b, int n_sweeps, int n_heatbath, int n_overrelax, double* plaq,
+                         double* poly);
+void sun_batch_destroy(sun_batch* b); /* syncs; the lattices are not touched */
 
 /* Plaquette of link storage the caller already holds, with no allocation.
  * The paper has no counterpart: this entry point exists for callers that

@@ -4,7 +4,8 @@ Chessboard heatbath / overrelaxation sweep of Cardoso & Bicudo,
 "Generating SU(Nc) pure gauge lattice QCD configurations on GPUs with CUDA"
 (arXiv:1112.4533), behind the C ABI of include/sun.h (libsun.so).
 """
-from .sun import (HEATBATH, OVERRELAX, Lattice, SunError, footprint_bytes, lattice_create,  # noqa: F401
+from .sun import (HEATBATH, OVERRELAX, Batch, Lattice, SunError, footprint_bytes, lattice_create,  # noqa: F401
                   load_library)
 
-__all__ = ["HEATBATH", "OVERRELAX", "Lattice", "SunError", "footprint_bytes", "lattice_create", "load_library"]
+__all__ = ["HEATBATH", "OVERRELAX", "Batch", "Lattice", "SunError", "footprint_bytes", "lattice_create",
+           "load_library"]

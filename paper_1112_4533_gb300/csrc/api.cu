@@ -8,9 +8,11 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <map>
 #include <string>
 #include <tuple>
+#include <vector>
 
 #include "sun.h"
 #include "sun_runtime.h"
@@ -300,6 +302,9 @@ static sun_status resolve(int nc, const int* dims, const sun_options* opt_in, su
   if (!*ops)
     return fail(SUN_ERR_UNSUPPORTED, "no kernels for nc = %d, storage = %d, precision = %d (built: nc 2..6)", nc,
                 opt->storage, opt->precision);
+  if (opt->reunit_mode != 0 && !(*ops)->fused_reunit)
+    return fail(SUN_ERR_UNSUPPORTED, "reunit_mode %d is not built for nc = %d at precision %d", opt->reunit_mode, nc,
+                opt->precision);
   return SUN_OK;
 }
 
@@ -612,6 +617,338 @@ sun_status sun_get_info(const sun_lattice* L, sun_lattice_info* info) {
   info->footprint = L->plan.total;
   info->links = L->ctx.links;
   info->stream = L->stream;
+  return SUN_OK;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Batches of chains
+// ===========================================================================
+namespace {
+
+__global__ void batch_bump_kernel(sun::ChainDesc* chains, int n, uint32_t hb_steps) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < n) *chains[c].hb_step += hb_steps;
+}
+
+__global__ void slot_bump_kernel(uint32_t* slot) { *slot += 1u; }
+
+struct BatchGroup {
+  const sun::Ops* ops = nullptr;
+  std::vector<sun_lattice*> members;
+  int offset = 0;  // position of the first member in the create call order of the batch table
+  std::vector<int> positions;  // create-call position of each member
+  sun::ChainDesc* d_chains = nullptr;
+  uint32_t* d_start = nullptr;  // pass, reunit, plaquette, Polyakov tables, n+1 each
+  double* d_partials = nullptr;
+  int* d_pos = nullptr;
+  sun::BatchCtx ctx{};
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+};
+
+}  // namespace
+
+struct sun_batch {
+  int n = 0;
+  int device = 0;
+  std::vector<sun_lattice*> lattices;
+  std::vector<BatchGroup> groups;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaStream_t capture_stream = nullptr;
+  cudaEvent_t fork = nullptr;
+  uint32_t* d_slot = nullptr;
+  double* d_hist = nullptr;  // [cap][n] plaquette, then [cap][n][2] Polyakov (group-ordered columns)
+  double* h_hist = nullptr;
+  int hist_cap = 0;
+  int reunit_every = 1, reunit_mode = 0;
+  uint64_t sweeps_done = 0;
+  int use_graphs = 1;
+  std::map<GraphKey, cudaGraphExec_t> graphs;
+};
+
+namespace {
+
+template <class T>
+sun_status dev_alloc(T** p, size_t count) {
+  void* q = nullptr;
+  if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(SUN_ERR_OOM, "cudaMalloc of %zu bytes for a batch table failed", count * sizeof(T));
+  }
+  *p = static_cast<T*>(q);
+  return SUN_OK;
+}
+
+sun_status enqueue_batch_sweep(sun_batch* B, cudaStream_t s, int n_hb, int n_or, bool reunit, bool plaq, bool poly,
+                               bool hist_mode) {
+  const int n_steps = n_hb + n_or;
+  const bool fused = reunit && B->reunit_mode != 0 && n_steps > 0;
+  SUN_CUDA(cudaEventRecord(B->fork, s));
+  for (auto& g : B->groups) {
+    SUN_CUDA(cudaStreamWaitEvent(g.stream, B->fork, 0));
+    sun::BatchCtx c = g.ctx;
+    c.stream = g.stream;
+    for (int step = 0; step < n_steps; ++step) {
+      const bool hb = step < n_hb;
+      uint32_t mod = 0, rem = 0;
+      if (fused && B->reunit_mode == 1 && step == n_steps - 1) mod = 1;
+      if (fused && B->reunit_mode == 2) {
+        mod = uint32_t(n_steps);
+        rem = uint32_t(step);
+      }
+      for (int mu = 0; mu < 4; ++mu)
+        for (int p = 0; p < 2; ++p)
+          SUN_TRY(check_launch(g.ops->batch_pass(c, hb ? SUN_HEATBATH : SUN_OVERRELAX, mu, p, hb ? uint32_t(step) : 0u,
+                                                 mod, rem),
+                               "batched pass"));
+    }
+    if (reunit && !fused) SUN_TRY(check_launch(g.ops->batch_reunit(c), "batched reunitarization"));
+    const uint32_t* slot = hist_mode ? B->d_slot : nullptr;
+    if (plaq) SUN_TRY(check_launch(g.ops->batch_plaquette(c, B->d_hist, slot, B->hist_cap, g.offset, B->n),
+                                   "batched plaquette"));
+    if (poly)
+      SUN_TRY(check_launch(g.ops->batch_polyakov(c, B->d_hist + size_t(B->hist_cap) * B->n, slot, B->hist_cap,
+                                                 g.offset, B->n),
+                           "batched polyakov"));
+    if (n_hb > 0) {
+      batch_bump_kernel<<<unsigned((g.ctx.n + 127) / 128), 128, 0, g.stream>>>(g.d_chains, g.ctx.n, uint32_t(n_hb));
+      SUN_TRY(check_launch(cudaGetLastError(), "batched step counter"));
+    }
+    SUN_CUDA(cudaEventRecord(g.done, g.stream));
+    SUN_CUDA(cudaStreamWaitEvent(s, g.done, 0));
+  }
+  if (hist_mode) {
+    slot_bump_kernel<<<1, 1, 0, s>>>(B->d_slot);
+    SUN_TRY(check_launch(cudaGetLastError(), "history slot"));
+  }
+  return SUN_OK;
+}
+
+sun_status get_batch_graph(sun_batch* B, const GraphKey& key, cudaGraphExec_t* out) {
+  auto it = B->graphs.find(key);
+  if (it != B->graphs.end()) {
+    *out = it->second;
+    return SUN_OK;
+  }
+  SUN_CUDA(cudaStreamBeginCapture(B->capture_stream, cudaStreamCaptureModeThreadLocal));
+  sun_status st = enqueue_batch_sweep(B, B->capture_stream, key.n_hb, key.n_or, key.reunit != 0, key.plaq != 0,
+                                      key.poly != 0, true);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(B->capture_stream, &g);
+  if (st != SUN_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return fail(SUN_ERR_CUDA, "batch graph capture failed: %s", cudaGetErrorString(e));
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(SUN_ERR_CUDA, "batch graph instantiation failed: %s", cudaGetErrorString(e));
+  B->graphs[key] = exec;
+  *out = exec;
+  return SUN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sun_status sun_batch_create(sun_batch** out, sun_lattice* const* lattices, int n, void* stream, int use_graphs) {
+  if (!out) return fail(SUN_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!lattices || n < 1) return fail(SUN_ERR_ARG, "a batch needs at least one lattice");
+  for (int i = 0; i < n; ++i)
+    if (!lattices[i]) return fail(SUN_ERR_ARG, "lattice %d is NULL", i);
+  const sun_lattice* L0 = lattices[0];
+  for (int i = 0; i < n; ++i) {
+    const sun_lattice* L = lattices[i];
+    if (L->device != L0->device) return fail(SUN_ERR_ARG, "all lattices of a batch must be on one device");
+    if (L->reunit_every > 1) return fail(SUN_ERR_ARG, "batched lattices need reunit_every 0 or 1");
+    if (L->reunit_every != L0->reunit_every || L->reunit_mode != L0->reunit_mode)
+      return fail(SUN_ERR_ARG, "batched lattices must share reunit_every and reunit_mode");
+    if (!L->ops->batch_pass)
+      return fail(SUN_ERR_UNSUPPORTED, "no batched kernels for nc = %d at precision %d", L->nc, L->precision);
+    for (int j = 0; j < i; ++j)
+      if (lattices[j] == L) return fail(SUN_ERR_ARG, "lattice %d appears twice", i);
+  }
+  sun_batch* B = new sun_batch();
+  auto cleanup = [&](sun_status st) {
+    sun_batch_destroy(B);
+    return st;
+  };
+  B->n = n;
+  B->device = L0->device;
+  B->lattices.assign(lattices, lattices + n);
+  B->reunit_every = L0->reunit_every;
+  B->reunit_mode = L0->reunit_mode;
+  B->use_graphs = use_graphs;
+  if (cudaSetDevice(B->device) != cudaSuccess) return cleanup(fail(SUN_ERR_CUDA, "cudaSetDevice failed"));
+
+  // groups in order of first appearance; members in create-call order
+  for (int i = 0; i < n; ++i) {
+    sun_lattice* L = lattices[i];
+    auto it = std::find_if(B->groups.begin(), B->groups.end(), [&](const BatchGroup& g) { return g.ops == L->ops; });
+    if (it == B->groups.end()) {
+      B->groups.emplace_back();
+      it = B->groups.end() - 1;
+      it->ops = L->ops;
+    }
+    it->members.push_back(L);
+    it->positions.push_back(i);
+  }
+  // history columns are group-ordered: column offset of each group
+  int col = 0;
+  for (auto& g : B->groups) {
+    g.offset = col;
+    col += int(g.members.size());
+  }
+  for (auto& g : B->groups) {
+    const int m = int(g.members.size());
+    const sun_lattice* first = g.members[0];
+    const int bt = (first->ctx.variant & 1) ? 128 : first->block_threads;
+    std::vector<sun::ChainDesc> desc(m);
+    std::vector<uint32_t> start(4 * (m + 1), 0);
+    uint64_t tot[4] = {0, 0, 0, 0};
+    for (int k = 0; k < m; ++k) {
+      const sun_lattice* L = g.members[k];
+      const sun::Geom& ge = L->ctx.g;
+      sun::ChainDesc& d = desc[k];
+      d.links = L->ctx.links;
+      d.block_bytes = L->ctx.block_bytes;
+      d.g = ge;
+      d.alpha_coef = 2.0 * L->beta / L->nc;
+      d.key = make_uint2(uint32_t(L->seed & 0xffffffffu), uint32_t(L->seed >> 32));
+      d.hb_step = &L->ctx.state->hb_step;
+      const int64_t nsp = int64_t(ge.nx) * ge.ny * ge.nz;
+      d.plaq_scale = 1.0 / (6.0 * double(ge.V) * L->nc);
+      d.poly_scale = 1.0 / (double(L->nc) * double(nsp));
+      const uint64_t blocks[4] = {uint64_t((ge.Vh + bt - 1) / bt), uint64_t((8 * ge.Vh + 127) / 128),
+                                  uint64_t((ge.V + 255) / 256), uint64_t((nsp + 127) / 128)};
+      for (int q = 0; q < 4; ++q) {
+        start[q * (m + 1) + k] = uint32_t(tot[q]);
+        tot[q] += blocks[q];
+      }
+    }
+    for (int q = 0; q < 4; ++q) {
+      if (tot[q] >= (uint64_t(1) << 31)) return cleanup(fail(SUN_ERR_ARG, "batch too large for one grid"));
+      start[q * (m + 1) + m] = uint32_t(tot[q]);
+    }
+    sun_status st;
+    if ((st = dev_alloc(&g.d_chains, size_t(m))) != SUN_OK) return cleanup(st);
+    if ((st = dev_alloc(&g.d_start, start.size())) != SUN_OK) return cleanup(st);
+    const size_t npart = std::max<size_t>(tot[2], 2 * tot[3]);
+    if ((st = dev_alloc(&g.d_partials, npart)) != SUN_OK) return cleanup(st);
+    if (cudaMemcpy(g.d_chains, desc.data(), m * sizeof(sun::ChainDesc), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(g.d_start, start.data(), start.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess)
+      return cleanup(fail(SUN_ERR_CUDA, "upload of a batch table failed"));
+    if (cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming) != cudaSuccess)
+      return cleanup(fail(SUN_ERR_CUDA, "batch stream creation failed"));
+    sun::BatchCtx& c = g.ctx;
+    c.chains = g.d_chains;
+    c.n = m;
+    c.pass_start = g.d_start;
+    c.reunit_start = g.d_start + (m + 1);
+    c.plaq_start = g.d_start + 2 * (m + 1);
+    c.poly_start = g.d_start + 3 * (m + 1);
+    c.pass_blocks = uint32_t(tot[0]);
+    c.reunit_blocks = uint32_t(tot[1]);
+    c.plaq_blocks = uint32_t(tot[2]);
+    c.poly_blocks = uint32_t(tot[3]);
+    c.pass_threads = bt;
+    c.variant = first->ctx.variant;
+    c.partials = g.d_partials;
+  }
+  if (stream) {
+    B->stream = static_cast<cudaStream_t>(stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking) != cudaSuccess)
+      return cleanup(fail(SUN_ERR_CUDA, "stream creation failed"));
+    B->own_stream = true;
+  }
+  if (cudaStreamCreateWithFlags(&B->capture_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming) != cudaSuccess)
+    return cleanup(fail(SUN_ERR_CUDA, "batch stream creation failed"));
+  B->hist_cap = int(std::max<int64_t>(1, std::min<int64_t>(kHistCap, (int64_t(4) << 20) / (3 * int64_t(n)))));
+  sun_status st;
+  if ((st = dev_alloc(&B->d_slot, 1)) != SUN_OK) return cleanup(st);
+  if ((st = dev_alloc(&B->d_hist, size_t(3) * B->hist_cap * n)) != SUN_OK) return cleanup(st);
+  if (cudaMallocHost(&B->h_hist, size_t(3) * B->hist_cap * n * sizeof(double)) != cudaSuccess)
+    return cleanup(fail(SUN_ERR_CUDA, "pinned history buffer allocation failed"));
+  *out = B;
+  return SUN_OK;
+}
+
+void sun_batch_destroy(sun_batch* B) {
+  if (!B) return;
+  cudaSetDevice(B->device);
+  if (B->stream) cudaStreamSynchronize(B->stream);
+  for (auto& kv : B->graphs) cudaGraphExecDestroy(kv.second);
+  for (auto& g : B->groups) {
+    if (g.stream) {
+      cudaStreamSynchronize(g.stream);
+      cudaStreamDestroy(g.stream);
+    }
+    if (g.done) cudaEventDestroy(g.done);
+    cudaFree(g.d_chains);
+    cudaFree(g.d_start);
+    cudaFree(g.d_partials);
+  }
+  if (B->fork) cudaEventDestroy(B->fork);
+  if (B->capture_stream) cudaStreamDestroy(B->capture_stream);
+  if (B->own_stream && B->stream) cudaStreamDestroy(B->stream);
+  cudaFree(B->d_slot);
+  cudaFree(B->d_hist);
+  if (B->h_hist) cudaFreeHost(B->h_hist);
+  delete B;
+}
+
+sun_status sun_batch_run(sun_batch* B, int n_sweeps, int n_hb, int n_or, double* plaq, double* poly) {
+  if (!B) return fail(SUN_ERR_ARG, "batch is NULL");
+  if (n_sweeps < 0 || n_hb < 0 || n_or < 0) return fail(SUN_ERR_ARG, "counts must be >= 0");
+  SUN_CUDA(cudaSetDevice(B->device));
+  for (sun_lattice* L : B->lattices) SUN_CUDA(cudaStreamSynchronize(L->stream));
+  const bool want_p = plaq != nullptr, want_l = poly != nullptr;
+  const int n = B->n;
+  for (int done = 0; done < n_sweeps;) {
+    const int chunk = std::min(n_sweeps - done, B->hist_cap);
+    SUN_CUDA(cudaMemsetAsync(B->d_slot, 0, sizeof(uint32_t), B->stream));
+    for (int k = 0; k < chunk; ++k) {
+      const bool reunit = B->reunit_every == 1;
+      if (B->use_graphs) {
+        cudaGraphExec_t exec = nullptr;
+        SUN_TRY(get_batch_graph(B, GraphKey{n_hb, n_or, reunit ? 1 : 0, want_p ? 1 : 0, want_l ? 1 : 0}, &exec));
+        SUN_CUDA(cudaGraphLaunch(exec, B->stream));
+      } else {
+        SUN_TRY(enqueue_batch_sweep(B, B->stream, n_hb, n_or, reunit, want_p, want_l, true));
+      }
+    }
+    if (want_p || want_l) {
+      SUN_CUDA(cudaMemcpyAsync(B->h_hist, B->d_hist, size_t(3) * B->hist_cap * n * sizeof(double),
+                               cudaMemcpyDeviceToHost, B->stream));
+      SUN_CUDA(cudaStreamSynchronize(B->stream));
+      // group-ordered columns back to create-call order
+      for (const auto& g : B->groups)
+        for (size_t k = 0; k < g.members.size(); ++k) {
+          const int colg = g.offset + int(k), pos = g.positions[k];
+          for (int r = 0; r < chunk; ++r) {
+            if (want_p) plaq[size_t(done + r) * n + pos] = B->h_hist[size_t(r) * n + colg];
+            if (want_l) {
+              const double* src = B->h_hist + size_t(B->hist_cap) * n + (size_t(r) * n + colg) * 2;
+              poly[(size_t(done + r) * n + pos) * 2] = src[0];
+              poly[(size_t(done + r) * n + pos) * 2 + 1] = src[1];
+            }
+          }
+        }
+    }
+    done += chunk;
+  }
+  SUN_CUDA(cudaStreamSynchronize(B->stream));
+  B->sweeps_done += uint64_t(n_sweeps);
+  for (sun_lattice* L : B->lattices) L->sweeps_done += uint64_t(n_sweeps);
   return SUN_OK;
 }
 

@@ -35,19 +35,22 @@ struct Cpx {
   R re, im;
 };
 
+// The library is compiled without floating-point contraction (-fmad=false), so
+// every kernel that inlines these helpers rounds identically; the products
+// below spell out their fused multiply-adds.
 template <class R>
 __device__ __forceinline__ Cpx<R> cmul(Cpx<R> a, Cpx<R> b) {
-  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+  return {fma(a.re, b.re, -(a.im * b.im)), fma(a.re, b.im, a.im * b.re)};
 }
 // a * conj(b)
 template <class R>
 __device__ __forceinline__ Cpx<R> cmulc(Cpx<R> a, Cpx<R> b) {
-  return {a.re * b.re + a.im * b.im, a.im * b.re - a.re * b.im};
+  return {fma(a.re, b.re, a.im * b.im), fma(a.im, b.re, -(a.re * b.im))};
 }
 // conj(a) * b
 template <class R>
 __device__ __forceinline__ Cpx<R> ccmul(Cpx<R> a, Cpx<R> b) {
-  return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
+  return {fma(a.re, b.re, a.im * b.im), fma(a.re, b.im, -(a.im * b.re))};
 }
 // acc += a * b
 template <class R>
@@ -196,11 +199,12 @@ struct Quat {
 // product p q of the matrices p, q
 template <class R>
 __device__ __forceinline__ Quat<R> qmul(Quat<R> p, Quat<R> q) {
+  // r0 = p0 q0 - p.q ; r = p0 q + q0 p - p x q
   Quat<R> r;
-  r.a0 = p.a0 * q.a0 - p.a1 * q.a1 - p.a2 * q.a2 - p.a3 * q.a3;
-  r.a1 = p.a0 * q.a1 + q.a0 * p.a1 - (p.a2 * q.a3 - p.a3 * q.a2);
-  r.a2 = p.a0 * q.a2 + q.a0 * p.a2 - (p.a3 * q.a1 - p.a1 * q.a3);
-  r.a3 = p.a0 * q.a3 + q.a0 * p.a3 - (p.a1 * q.a2 - p.a2 * q.a1);
+  r.a0 = fma(p.a0, q.a0, -fma(p.a1, q.a1, fma(p.a2, q.a2, p.a3 * q.a3)));
+  r.a1 = fma(p.a0, q.a1, fma(q.a0, p.a1, fma(p.a3, q.a2, -(p.a2 * q.a3))));
+  r.a2 = fma(p.a0, q.a2, fma(q.a0, p.a2, fma(p.a1, q.a3, -(p.a3 * q.a1))));
+  r.a3 = fma(p.a0, q.a3, fma(q.a0, p.a3, fma(p.a2, q.a1, -(p.a1 * q.a2))));
   return r;
 }
 template <class R>

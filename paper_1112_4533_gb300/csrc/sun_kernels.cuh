@@ -349,7 +349,7 @@ __device__ __forceinline__ void pass_body(const PassParams& p, int64_t h) {
     for (int j = i + 1; j < N; ++j) {
       const bool last = (i == N - 2) && (j == N - 1);
       const Quat<R> v = block_to_quat(w.e[i][i], w.e[i][j], w.e[j][i], w.e[j][j]);
-      const R k = d_sqrt(v.a0 * v.a0 + v.a1 * v.a1 + v.a2 * v.a2 + v.a3 * v.a3);
+      const R k = d_sqrt(fma(v.a0, v.a0, fma(v.a1, v.a1, fma(v.a2, v.a2, v.a3 * v.a3))));
       if (k > R(1e-15) && d_isfinite(k)) {
         const R inv = R(1) / k;
         const Quat<R> vd = {v.a0 * inv, -v.a1 * inv, -v.a2 * inv, -v.a3 * inv};  // vhat^+
@@ -398,6 +398,13 @@ __global__ void __launch_bounds__(128, 6) update_pass_mat_occ(const PassParams p
   pass_body<R, N, S, MODE, (VAR & 2) != 0, REUNIT>(p, h);
 }
 
+// FP64 passes of Nc >= 5 are built without the fused re-unitarization
+// (reunit_mode 1, 2): they would double the largest units' build time.
+template <class R, int N>
+constexpr bool has_fused_reunit() {
+  return !(std::is_same<R, double>::value && N >= 5);
+}
+
 // kernel variants are built for the SU(3) FP32 update passes only
 template <class R, int N, int S>
 constexpr bool has_variants() {
@@ -409,10 +416,8 @@ constexpr bool has_variants() {
 // with the staple kept in the real span of SU(2).
 // ---------------------------------------------------------------------------
 template <class R, int MODE, bool REUNIT>
-__global__ void __launch_bounds__(kMaxBlockThreads) update_pass_quat(const PassParams p) {
-  const int64_t h = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void quat_pass_body(const PassParams& p, int64_t h) {
   const Geom& g = p.g;
-  if (h >= g.Vh) return;
   const int mu = p.mu, par = p.parity, opp = par ^ 1;
   const Site s = decode_half(g, h, par);
   const uint32_t lex = uint32_t(s.lex);
@@ -443,7 +448,7 @@ __global__ void __launch_bounds__(kMaxBlockThreads) update_pass_quat(const PassP
   char* ublk = p.links + (2 * mu + par) * p.block_bytes;
   Quat<R> u = load_quat<R, false>(ublk, g.Vh, h);
   const Quat<R> w = qmul(u, qdag(st));
-  const R k = d_sqrt(w.a0 * w.a0 + w.a1 * w.a1 + w.a2 * w.a2 + w.a3 * w.a3);
+  const R k = d_sqrt(fma(w.a0, w.a0, fma(w.a1, w.a1, fma(w.a2, w.a2, w.a3 * w.a3))));
   if (k > R(1e-15) && d_isfinite(k)) {
     const R inv = R(1) / k;
     const Quat<R> vd = {w.a0 * inv, -w.a1 * inv, -w.a2 * inv, -w.a3 * inv};
@@ -464,6 +469,13 @@ __global__ void __launch_bounds__(kMaxBlockThreads) update_pass_quat(const PassP
     }
   }
   store_quat<R>(ublk, g.Vh, h, u);
+}
+
+template <class R, int MODE, bool REUNIT>
+__global__ void __launch_bounds__(kMaxBlockThreads) update_pass_quat(const PassParams p) {
+  const int64_t h = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (h >= p.g.Vh) return;
+  quat_pass_body<R, MODE, REUNIT>(p, h);
 }
 
 struct LinkParams {
@@ -600,82 +612,271 @@ __device__ __forceinline__ const char* obs_block(const ObsParams& p, int d, int 
   return p.links + (2 * d + par) * p.block_bytes;
 }
 
-// <P>: every site, the six plaquettes P_{mu nu}(x) = U_mu(x) U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+
-// (Eq. 4), ReTr in the storage precision, accumulated in FP64.
+// Sum over the six plaquettes P_{mu nu}(x) = U_mu(x) U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+
+// (Eq. 4) of one site (idx < V in parity-block order), ReTr in the storage
+// precision, each added in FP64.
 template <class R, int N, int S>
-__global__ void __launch_bounds__(256) plaquette_kernel(const ObsParams p, const ReduceParams rp) {
+__device__ __forceinline__ double site_plaquette(const ObsParams& p, int64_t idx) {
   const Geom& g = p.g;
-  double acc[1] = {0.0};
-  for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < g.V;
-       idx += int64_t(gridDim.x) * blockDim.x) {
-    const int par = idx >= g.Vh ? 1 : 0;
-    const int64_t h = idx - par * g.Vh;
-    const Site s = decode_half(g, h, par);
-    const uint32_t lex = uint32_t(s.lex);
+  const int par = idx >= g.Vh ? 1 : 0;
+  const int64_t h = idx - par * g.Vh;
+  const Site s = decode_half(g, h, par);
+  const uint32_t lex = uint32_t(s.lex);
+  double acc = 0.0;
 #pragma unroll
-    for (int mu = 0; mu < 3; ++mu) {
-      const int64_t xpmu = fwd(g, lex, s.c[mu], mu) >> 1;
-      if constexpr (S == kQuat) {
-        const Quat<R> umx = load_quat<R>(obs_block(p, mu, par), g.Vh, h);
+  for (int mu = 0; mu < 3; ++mu) {
+    const int64_t xpmu = fwd(g, lex, s.c[mu], mu) >> 1;
+    if constexpr (S == kQuat) {
+      const Quat<R> umx = load_quat<R>(obs_block(p, mu, par), g.Vh, h);
 #pragma unroll
-        for (int nu = mu + 1; nu < 4; ++nu) {
-          const int64_t xpnu = fwd(g, lex, s.c[nu], nu) >> 1;
-          const Quat<R> unx = load_quat<R>(obs_block(p, nu, par), g.Vh, h);
-          const Quat<R> t1 = qmul(umx, load_quat<R>(obs_block(p, nu, par ^ 1), g.Vh, xpmu));
-          const Quat<R> t2 = qmul(unx, load_quat<R>(obs_block(p, mu, par ^ 1), g.Vh, xpnu));
-          acc[0] += double(R(2) * (t1.a0 * t2.a0 + t1.a1 * t2.a1 + t1.a2 * t2.a2 + t1.a3 * t2.a3));
-        }
-      } else {
-        const Mat<R, N> umx = load_mat<R, N, S>(obs_block(p, mu, par), g.Vh, h);
+      for (int nu = mu + 1; nu < 4; ++nu) {
+        const int64_t xpnu = fwd(g, lex, s.c[nu], nu) >> 1;
+        const Quat<R> unx = load_quat<R>(obs_block(p, nu, par), g.Vh, h);
+        const Quat<R> t1 = qmul(umx, load_quat<R>(obs_block(p, nu, par ^ 1), g.Vh, xpmu));
+        const Quat<R> t2 = qmul(unx, load_quat<R>(obs_block(p, mu, par ^ 1), g.Vh, xpnu));
+        acc += double(R(2) * (t1.a0 * t2.a0 + t1.a1 * t2.a1 + t1.a2 * t2.a2 + t1.a3 * t2.a3));
+      }
+    } else {
+      const Mat<R, N> umx = load_mat<R, N, S>(obs_block(p, mu, par), g.Vh, h);
 #pragma unroll
-        for (int nu = mu + 1; nu < 4; ++nu) {
-          const int64_t xpnu = fwd(g, lex, s.c[nu], nu) >> 1;
-          const Mat<R, N> t1 = mul_nn(umx, load_mat<R, N, S>(obs_block(p, nu, par ^ 1), g.Vh, xpmu));
-          const Mat<R, N> t2 = mul_nn(load_mat<R, N, S>(obs_block(p, nu, par), g.Vh, h),
-                                      load_mat<R, N, S>(obs_block(p, mu, par ^ 1), g.Vh, xpnu));
-          acc[0] += double(retr_nd(t1, t2));
-        }
+      for (int nu = mu + 1; nu < 4; ++nu) {
+        const int64_t xpnu = fwd(g, lex, s.c[nu], nu) >> 1;
+        const Mat<R, N> t1 = mul_nn(umx, load_mat<R, N, S>(obs_block(p, nu, par ^ 1), g.Vh, xpmu));
+        const Mat<R, N> t2 = mul_nn(load_mat<R, N, S>(obs_block(p, nu, par), g.Vh, h),
+                                    load_mat<R, N, S>(obs_block(p, mu, par ^ 1), g.Vh, xpnu));
+        acc += double(retr_nd(t1, t2));
       }
     }
   }
+  return acc;
+}
+
+// Tr of the ordered product of U_t over t at spatial site xs (products in the
+// storage precision, trace returned in FP64).
+template <class R, int N, int S>
+__device__ __forceinline__ void site_polyakov(const ObsParams& p, int64_t xs, double& re, double& im) {
+  const Geom& g = p.g;
+  const int64_t nsp = int64_t(g.nx) * g.ny * g.nz;
+  const int x = int(xs % g.nx);
+  const int y = int((xs / g.nx) % g.ny);
+  const int z = int(xs / (int64_t(g.nx) * g.ny));
+  const int sp = (x + y + z) & 1;
+  re = 0.0;
+  im = 0.0;
+  if constexpr (S == kQuat) {
+    Quat<R> P = load_quat<R>(obs_block(p, 3, sp), g.Vh, xs >> 1);
+    for (int t = 1; t < g.nt; ++t) {
+      const int64_t lex = xs + int64_t(t) * nsp;
+      P = qmul(P, load_quat<R>(obs_block(p, 3, (sp + t) & 1), g.Vh, lex >> 1));
+    }
+    re = double(R(2) * P.a0);  // Tr of [[a0 + i a3, .], [., a0 - i a3]] is real
+  } else {
+    Mat<R, N> P = load_mat<R, N, S>(obs_block(p, 3, sp), g.Vh, xs >> 1);
+    for (int t = 1; t < g.nt; ++t) {
+      const int64_t lex = xs + int64_t(t) * nsp;
+      P = mul_nn(P, load_mat<R, N, S>(obs_block(p, 3, (sp + t) & 1), g.Vh, lex >> 1));
+    }
+#pragma unroll
+    for (int d = 0; d < N; ++d) {
+      re += double(P.e[d][d].re);
+      im += double(P.e[d][d].im);
+    }
+  }
+}
+
+// <P> of one lattice: grid-stride over sites, deterministic FP64 reduction.
+template <class R, int N, int S>
+__global__ void __launch_bounds__(256) plaquette_kernel(const ObsParams p, const ReduceParams rp) {
+  double acc[1] = {0.0};
+  for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < p.g.V;
+       idx += int64_t(gridDim.x) * blockDim.x)
+    acc[0] += site_plaquette<R, N, S>(p, idx);
   reduce_finish<1>(acc, rp);
 }
 
-// Polyakov loop: every spatial site, Tr of the ordered product of U_t over t,
-// products in the storage precision, accumulated in FP64 (re, im).
+// Polyakov loop of one lattice: grid-stride over spatial sites, FP64 (re, im).
 template <class R, int N, int S>
 __global__ void __launch_bounds__(256) polyakov_kernel(const ObsParams p, const ReduceParams rp) {
-  const Geom& g = p.g;
-  const int64_t nsp = int64_t(g.nx) * g.ny * g.nz;
+  const int64_t nsp = int64_t(p.g.nx) * p.g.ny * p.g.nz;
   double acc[2] = {0.0, 0.0};
   for (int64_t xs = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; xs < nsp;
        xs += int64_t(gridDim.x) * blockDim.x) {
-    const int x = int(xs % g.nx);
-    const int y = int((xs / g.nx) % g.ny);
-    const int z = int(xs / (int64_t(g.nx) * g.ny));
-    const int sp = (x + y + z) & 1;
-    if constexpr (S == kQuat) {
-      Quat<R> P = load_quat<R>(obs_block(p, 3, sp), g.Vh, xs >> 1);
-      for (int t = 1; t < g.nt; ++t) {
-        const int64_t lex = xs + int64_t(t) * nsp;
-        P = qmul(P, load_quat<R>(obs_block(p, 3, (sp + t) & 1), g.Vh, lex >> 1));
-      }
-      acc[0] += double(R(2) * P.a0);  // Tr of [[a0 + i a3, .], [., a0 - i a3]] is real
-    } else {
-      Mat<R, N> P = load_mat<R, N, S>(obs_block(p, 3, sp), g.Vh, xs >> 1);
-      for (int t = 1; t < g.nt; ++t) {
-        const int64_t lex = xs + int64_t(t) * nsp;
-        P = mul_nn(P, load_mat<R, N, S>(obs_block(p, 3, (sp + t) & 1), g.Vh, lex >> 1));
-      }
-#pragma unroll
-      for (int d = 0; d < N; ++d) {
-        acc[0] += double(P.e[d][d].re);
-        acc[1] += double(P.e[d][d].im);
-      }
-    }
+    double re, im;
+    site_polyakov<R, N, S>(p, xs, re, im);
+    acc[0] += re;
+    acc[1] += im;
   }
   reduce_finish<2>(acc, rp);
 }
+
+// ---------------------------------------------------------------------------
+// Batched kernels: many independent lattices ("chains") of one (Nc, storage,
+// precision) in one launch.  Block b belongs to chain c with
+// start[c] <= b < start[c+1]; thread 0 finds c and stages the chain's
+// parameters in shared memory for the block.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int find_chain(const uint32_t* start, int n, uint32_t b) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (start[mid] <= b)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+template <class R, int N, int S, int MODE, int VAR, bool REUNIT>
+__device__ __forceinline__ void batch_pass_body(const BatchParams& bp, int mu, int parity, uint32_t step_offset,
+                                                uint32_t rmod, uint32_t rrem) {
+  __shared__ PassParams sp;
+  __shared__ uint32_t first;
+  if (threadIdx.x == 0) {
+    const int c = find_chain(bp.start, bp.n, blockIdx.x);
+    const ChainDesc& d = bp.chains[c];
+    first = bp.start[c];
+    sp.links = d.links;
+    sp.block_bytes = d.block_bytes;
+    sp.g = d.g;
+    sp.mu = mu;
+    sp.parity = parity;
+    sp.alpha_coef = d.alpha_coef;
+    sp.key = d.key;
+    sp.hb_step = d.hb_step;
+    sp.step_offset = step_offset;
+    sp.reunit_mod = rmod;
+    sp.reunit_rem = rrem;
+  }
+  __syncthreads();
+  const int64_t h = int64_t(blockIdx.x - first) * blockDim.x + threadIdx.x;
+  if (h >= sp.g.Vh) return;
+  if constexpr (S == kQuat)
+    quat_pass_body<R, MODE, REUNIT>(sp, h);
+  else
+    pass_body<R, N, S, MODE, (VAR & 2) != 0, REUNIT>(sp, h);
+}
+
+template <class R, int N, int S, int MODE, int VAR, bool REUNIT>
+__global__ void __launch_bounds__(kMaxBlockThreads)
+    update_pass_batch(const BatchParams bp, int mu, int parity, uint32_t step_offset, uint32_t rmod, uint32_t rrem) {
+  batch_pass_body<R, N, S, MODE, VAR, REUNIT>(bp, mu, parity, step_offset, rmod, rrem);
+}
+
+template <class R, int N, int S, int MODE, int VAR, bool REUNIT>
+__global__ void __launch_bounds__(128, 6)
+    update_pass_batch_occ(const BatchParams bp, int mu, int parity, uint32_t step_offset, uint32_t rmod,
+                          uint32_t rrem) {
+  batch_pass_body<R, N, S, MODE, VAR, REUNIT>(bp, mu, parity, step_offset, rmod, rrem);
+}
+
+// stage the chain's observable parameters of this block in shared memory
+__device__ __forceinline__ void batch_obs_chain(const BatchParams& bp, ObsParams& sp, uint32_t& first) {
+  if (threadIdx.x == 0) {
+    const int c = find_chain(bp.start, bp.n, blockIdx.x);
+    const ChainDesc& d = bp.chains[c];
+    first = bp.start[c];
+    sp.links = d.links;
+    sp.block_bytes = d.block_bytes;
+    sp.g = d.g;
+  }
+  __syncthreads();
+}
+
+template <class R, int N, int S>
+__global__ void __launch_bounds__(128) reunit_batch(const BatchParams bp) {
+  __shared__ ObsParams sp;
+  __shared__ uint32_t first;
+  batch_obs_chain(bp, sp, first);
+  const int64_t idx = int64_t(blockIdx.x - first) * blockDim.x + threadIdx.x;
+  if (idx >= 8 * sp.g.Vh) return;
+  const int b = int(idx / sp.g.Vh);
+  const int64_t h = idx - int64_t(b) * sp.g.Vh;
+  char* blk = const_cast<char*>(sp.links) + b * sp.block_bytes;
+  if constexpr (S == kQuat) {
+    const Quat<R> q = load_quat<R, false>(blk, sp.g.Vh, h);
+    const double a0 = q.a0, a1 = q.a1, a2 = q.a2, a3 = q.a3;
+    const double inv = rsqrt(a0 * a0 + a3 * a3 + a2 * a2 + a1 * a1);
+    store_quat<R>(blk, sp.g.Vh, h, Quat<R>{R(a0 * inv), R(a1 * inv), R(a2 * inv), R(a3 * inv)});
+  } else {
+    Mat<double, N> m = mat_cast<R, double, N>(load_mat<R, N, S, false>(blk, sp.g.Vh, h));
+    reunit_d<N>(m);
+    store_mat<R, N, S>(blk, sp.g.Vh, h, mat_cast<double, R, N>(m));
+  }
+}
+
+// sum of v over the block into thread 0 (warp shuffles, then shared memory)
+template <int K>
+__device__ __forceinline__ void block_sum(double (&v)[K]) {
+  __shared__ double sh[kMaxBlockThreads / 32][K];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    if (lane == 0) sh[warp][k] = v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double s = 0.0;
+      for (int w = 0; w < nwarps; ++w) s += sh[w][k];
+      v[k] = s;
+    }
+  }
+}
+
+// per-block partial <P> sums, one block per 256 sites of a chain
+template <class R, int N, int S>
+__global__ void __launch_bounds__(256) plaquette_batch(const BatchParams bp, double* partials) {
+  __shared__ ObsParams sp;
+  __shared__ uint32_t first;
+  batch_obs_chain(bp, sp, first);
+  const int64_t idx = int64_t(blockIdx.x - first) * blockDim.x + threadIdx.x;
+  double v[1] = {idx < sp.g.V ? site_plaquette<R, N, S>(sp, idx) : 0.0};
+  block_sum<1>(v);
+  if (threadIdx.x == 0) partials[blockIdx.x] = v[0];
+}
+
+// per-block partial Polyakov sums, one block per 128 spatial sites of a chain
+template <class R, int N, int S>
+__global__ void __launch_bounds__(128) polyakov_batch(const BatchParams bp, double* partials) {
+  __shared__ ObsParams sp;
+  __shared__ uint32_t first;
+  batch_obs_chain(bp, sp, first);
+  const int64_t xs = int64_t(blockIdx.x - first) * blockDim.x + threadIdx.x;
+  double v[2] = {0.0, 0.0};
+  if (xs < int64_t(sp.g.nx) * sp.g.ny * sp.g.nz) site_polyakov<R, N, S>(sp, xs, v[0], v[1]);
+  block_sum<2>(v);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = v[0];
+    partials[2 * blockIdx.x + 1] = v[1];
+  }
+}
+
+// One warp per chain adds the chain's block partials in a fixed order and
+// writes out[(slot % cap) * stride + offset + c] (K values per chain).
+template <int K>
+__global__ void __launch_bounds__(32) batch_finish(const BatchParams bp, const double* partials, int which,
+                                                   double* out, const uint32_t* slot, int cap, int offset,
+                                                   int stride) {
+  const int c = blockIdx.x;
+  const int lane = threadIdx.x;
+  const uint32_t b0 = bp.start[c], b1 = bp.start[c + 1];
+  const ChainDesc& d = bp.chains[c];
+  const double scale = which == 0 ? d.plaq_scale : d.poly_scale;
+  const int row = slot ? int(*slot % uint32_t(cap)) : 0;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double s = 0.0;
+    for (uint32_t b = b0 + lane; b < b1; b += 32) s += partials[b * K + k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) out[(int64_t(row) * stride + offset + c) * K + k] = s * scale;
+  }
+}
+
 
 // ---------------------------------------------------------------------------
 // Canonical FP64 <-> storage conversion of links [first, first + count),
@@ -786,7 +987,13 @@ cudaError_t launch_pass(const Ctx& c, int mode, int mu, int parity, uint32_t ste
   const int bt = c.block_threads;
   const unsigned grid = unsigned((c.g.Vh + bt - 1) / bt);
   const bool ru = reunit_mod != 0u;
-  if constexpr (S == kQuat) {
+  if constexpr (!has_fused_reunit<R, N>()) {
+    if (ru) return cudaErrorNotSupported;
+    if (mode == kHeatbathMode)
+      update_pass_mat<R, N, S, kHeatbathMode, 0, false><<<grid, bt, 0, c.stream>>>(p);
+    else
+      update_pass_mat<R, N, S, kOverrelaxMode, 0, false><<<grid, bt, 0, c.stream>>>(p);
+  } else if constexpr (S == kQuat) {
 #define SUN_LAUNCH_QUAT(RU)                                                             \
   if (mode == kHeatbathMode)                                                            \
     update_pass_quat<R, kHeatbathMode, RU><<<grid, bt, 0, c.stream>>>(p);               \
@@ -921,12 +1128,79 @@ cudaError_t launch_import(const Ctx& c, const double* src, int64_t first, int64_
 }
 
 template <class R, int N, int S>
+cudaError_t launch_batch_pass(const BatchCtx& b, int mode, int mu, int parity, uint32_t so, uint32_t rmod,
+                              uint32_t rrem) {
+  if (b.n == 0) return cudaSuccess;
+  const BatchParams bp{b.chains, b.pass_start, b.n};
+  const bool ru = rmod != 0u;
+  const unsigned g1 = b.pass_blocks, bt = unsigned(b.pass_threads);
+#define SUN_LAUNCH_BATCH(K, V)                                                              \
+  if (mode == kHeatbathMode) {                                                              \
+    if (ru)                                                                                 \
+      K<R, N, S, kHeatbathMode, V, true><<<g1, bt, 0, b.stream>>>(bp, mu, parity, so, rmod, rrem);   \
+    else                                                                                    \
+      K<R, N, S, kHeatbathMode, V, false><<<g1, bt, 0, b.stream>>>(bp, mu, parity, so, rmod, rrem);  \
+  } else {                                                                                  \
+    if (ru)                                                                                 \
+      K<R, N, S, kOverrelaxMode, V, true><<<g1, bt, 0, b.stream>>>(bp, mu, parity, so, rmod, rrem);  \
+    else                                                                                    \
+      K<R, N, S, kOverrelaxMode, V, false><<<g1, bt, 0, b.stream>>>(bp, mu, parity, so, rmod, rrem); \
+  }
+  if constexpr (has_variants<R, N, S>()) {
+    if (b.variant & 1) {
+      SUN_LAUNCH_BATCH(update_pass_batch_occ, 1)
+    } else {
+      SUN_LAUNCH_BATCH(update_pass_batch, 0)
+    }
+  } else {
+    SUN_LAUNCH_BATCH(update_pass_batch, 0)
+  }
+#undef SUN_LAUNCH_BATCH
+  return cudaGetLastError();
+}
+
+template <class R, int N, int S>
+cudaError_t launch_batch_reunit(const BatchCtx& b) {
+  if (b.n == 0) return cudaSuccess;
+  reunit_batch<R, N, S><<<b.reunit_blocks, 128, 0, b.stream>>>(BatchParams{b.chains, b.reunit_start, b.n});
+  return cudaGetLastError();
+}
+
+template <class R, int N, int S>
+cudaError_t launch_batch_plaquette(const BatchCtx& b, double* out, const uint32_t* slot, int cap, int offset,
+                                   int stride) {
+  if (b.n == 0) return cudaSuccess;
+  const BatchParams bp{b.chains, b.plaq_start, b.n};
+  plaquette_batch<R, N, S><<<b.plaq_blocks, 256, 0, b.stream>>>(bp, b.partials);
+  batch_finish<1><<<unsigned(b.n), 32, 0, b.stream>>>(bp, b.partials, 0, out, slot, cap, offset, stride);
+  return cudaGetLastError();
+}
+
+template <class R, int N, int S>
+cudaError_t launch_batch_polyakov(const BatchCtx& b, double* out, const uint32_t* slot, int cap, int offset,
+                                  int stride) {
+  if (b.n == 0) return cudaSuccess;
+  const BatchParams bp{b.chains, b.poly_start, b.n};
+  polyakov_batch<R, N, S><<<b.poly_blocks, 128, 0, b.stream>>>(bp, b.partials);
+  batch_finish<2><<<unsigned(b.n), 32, 0, b.stream>>>(bp, b.partials, 1, out, slot, cap, offset, stride);
+  return cudaGetLastError();
+}
+
+// Batched kernels are built for FP32 and for Nc <= 3 (serving runs FP32; FP64
+// batches of large Nc cost build time without a use).
+template <class R, int N, int S>
+constexpr bool has_batch() {
+  return std::is_same<R, float>::value || N <= 3;
+}
+
+template <class R, int N, int S>
 const Ops* ops_instance() {
   static const Ops ops = {
       N,
       Layout<R, N, S>::nreals,
       int(sizeof(R)) * 8,
       Layout<R, N, S>::bytes,
+      has_fused_reunit<R, N>() ? 1 : 0,
       &launch_pass<R, N, S>,
       &launch_init<R, N, S>,
       &launch_reunit<R, N, S>,
@@ -934,6 +1208,10 @@ const Ops* ops_instance() {
       &launch_polyakov<R, N, S>,
       &launch_export<R, N, S>,
       &launch_import<R, N, S>,
+      has_batch<R, N, S>() ? &launch_batch_pass<R, N, S> : nullptr,
+      has_batch<R, N, S>() ? &launch_batch_reunit<R, N, S> : nullptr,
+      has_batch<R, N, S>() ? &launch_batch_plaquette<R, N, S> : nullptr,
+      has_batch<R, N, S>() ? &launch_batch_polyakov<R, N, S> : nullptr,
   };
   return &ops;
 }

@@ -60,9 +60,45 @@ struct Ctx {
   int variant;  // update-pass kernel variant (bit 0: 6 blocks/SM register bound, bit 1: two-row staple)
 };
 
+// One chain (lattice) of a batch, as the batched kernels read it.
+struct ChainDesc {
+  char* links;
+  int64_t block_bytes;
+  Geom g;
+  double alpha_coef;   // 2 beta / Nc
+  uint2 key;           // Philox key (seed)
+  uint32_t* hb_step;   // the chain's device heatbath step counter
+  double plaq_scale;   // 1 / (6 V Nc)
+  double poly_scale;   // 1 / (Nc Nx Ny Nz)
+};
+
+// Kernel-side view of a batch for one kernel kind: block b belongs to chain c
+// with start[c] <= b < start[c+1].
+struct BatchParams {
+  const ChainDesc* chains;
+  const uint32_t* start;
+  int n;
+};
+
+// Everything a batched launcher needs (device tables of one group of chains).
+struct BatchCtx {
+  const ChainDesc* chains;
+  int n;
+  const uint32_t* pass_start;
+  const uint32_t* reunit_start;
+  const uint32_t* plaq_start;
+  const uint32_t* poly_start;
+  uint32_t pass_blocks, reunit_blocks, plaq_blocks, poly_blocks;
+  int pass_threads;  // block size the pass table was built for
+  int variant;
+  double* partials;  // >= max(plaq_blocks, 2 * poly_blocks) doubles
+  cudaStream_t stream;
+};
+
 // The operations of one (Nc, storage, precision) combination.
 struct Ops {
   int nc, storage, precision, link_bytes;
+  int fused_reunit;  // reunit_mode 1 and 2 built
   cudaError_t (*pass)(const Ctx&, int mode, int mu, int parity, uint32_t step_offset, uint32_t reunit_mod,
                       uint32_t reunit_rem);
   cudaError_t (*init)(const Ctx&, int hot);
@@ -71,13 +107,27 @@ struct Ops {
   cudaError_t (*polyakov)(const Ctx&, double* out, const uint32_t* slot, int cap);
   cudaError_t (*export_links)(const Ctx&, double* dst, int64_t first, int64_t count);
   cudaError_t (*import_links)(const Ctx&, const double* src, int64_t first, int64_t count);
+  cudaError_t (*batch_pass)(const BatchCtx&, int mode, int mu, int parity, uint32_t step_offset, uint32_t reunit_mod,
+                            uint32_t reunit_rem);
+  cudaError_t (*batch_reunit)(const BatchCtx&);
+  // per-chain results to out[((*slot % cap) * stride + offset + c) * K + k]
+  cudaError_t (*batch_plaquette)(const BatchCtx&, double* out, const uint32_t* slot, int cap, int offset, int stride);
+  cudaError_t (*batch_polyakov)(const BatchCtx&, double* out, const uint32_t* slot, int cap, int offset, int stride);
 };
 
 const Ops* ops_su2(int storage, int precision);
 const Ops* ops_su3(int storage, int precision);
+const Ops* ops_su3_two_row(int precision);
+const Ops* ops_su3_full(int precision);
 const Ops* ops_su4(int storage, int precision);
 const Ops* ops_su5(int storage, int precision);
 const Ops* ops_su6(int storage, int precision);
+const Ops* ops_su4_f32();
+const Ops* ops_su4_f64();
+const Ops* ops_su5_f32();
+const Ops* ops_su5_f64();
+const Ops* ops_su6_f32();
+const Ops* ops_su6_f64();
 
 // sets the calling thread's sun_last_error() message
 void set_last_error_message(const char* msg);

@@ -1,0 +1,173 @@
+"""Continuous-batching server of configuration-generation requests.
+
+A request asks for n_sweeps sweeps (1 heatbath + n_overrelax overrelaxation
+steps, re-unitarization) of an SU(Nc) chain on an L^4 lattice from a Haar
+start, and gets back its plaquette and Polyakov-loop history.  The server keeps
+every admitted chain's links and random state (seed, heatbath counter) resident
+on the GPU, admits waiting requests in arrival order as soon as their device
+footprint fits the memory budget, and advances all admitted chains together:
+each tick is one batched run (sun_batch_run) over every active chain, chains of
+different Nc on their own streams.  Requests that arrive while others are on
+the GPU join at the next tick; finished chains leave and free their memory.
+
+The plain path (serve_plain) runs the same trace one request at a time, each
+chain alone (sun_run), in arrival order.
+"""
+import dataclasses
+import time
+from typing import List, Optional
+
+import numpy as np
+
+from . import sun
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    nc: int
+    L: int
+    beta: float
+    n_sweeps: int
+    seed: int
+    arrival: float  # seconds after the start of the trace
+    t_admit: Optional[float] = None
+    t_done: Optional[float] = None
+    plaquette: Optional[np.ndarray] = None
+    polyakov: Optional[np.ndarray] = None
+
+    @property
+    def dims(self):
+        return (self.L, self.L, self.L, self.L)
+
+    @property
+    def latency(self):
+        return None if self.t_done is None else self.t_done - self.arrival
+
+
+def poisson_trace(n, rate=20.0, seed=0, ncs=(2, 3, 4, 6), Ls=(8, 12, 16, 20, 24), sweeps=(20, 200)):
+    """n requests with exponential inter-arrival times of mean 1/rate; Nc and L
+    uniform over the given sets; beta uniform in [2.2, 2.5] for SU(2) and
+    0.7 Nc^2 x U[0.95, 1.05] otherwise; n_sweeps uniform in the given range."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for i in range(n):
+        t += rng.exponential(1.0 / rate)
+        nc = int(rng.choice(ncs))
+        L = int(rng.choice(Ls))
+        beta = float(rng.uniform(2.2, 2.5)) if nc == 2 else float(0.7 * nc * nc * rng.uniform(0.95, 1.05))
+        ns = int(rng.integers(sweeps[0], sweeps[1] + 1))
+        out.append(Request(i, nc, L, beta, ns, 1000 + i, t))
+    return out
+
+
+def _clone(reqs):
+    return [dataclasses.replace(r, t_admit=None, t_done=None, plaquette=None, polyakov=None) for r in reqs]
+
+
+def footprint(req, precision=32):
+    return sun.footprint_bytes(req.nc, req.dims, precision, 0)
+
+
+class Server:
+    """Continuous batching over a device-memory budget (bytes)."""
+
+    def __init__(self, hbm_budget, n_overrelax=4, sweeps_per_tick=2, precision=32, use_graphs=False,
+                 clock=time.perf_counter):
+        self.budget = int(hbm_budget)
+        self.n_or = int(n_overrelax)
+        self.k = int(sweeps_per_tick)
+        self.precision = precision
+        self.use_graphs = use_graphs
+        self.clock = clock
+        self.ticks = 0
+        self.link_updates = 0
+
+    def run(self, trace: List[Request]):
+        """Serve the trace in real time; returns the requests with their results."""
+        import torch
+
+        reqs = _clone(trace)
+        pending = sorted(reqs, key=lambda r: r.arrival)
+        active = []  # [request, lattice, sweeps done, plaquette list, polyakov list, footprint]
+        used = 0
+        batch = None
+        members = None
+        t0 = self.clock()
+        while pending or active:
+            now = self.clock() - t0
+            # admit in arrival order while the head of the queue fits the budget
+            while pending and pending[0].arrival <= now and used + footprint(pending[0], self.precision) <= self.budget:
+                r = pending.pop(0)
+                fp = footprint(r, self.precision)
+                lat = sun.Lattice(r.nc, r.dims, r.beta, hot_start=True, seed=r.seed, precision=self.precision)
+                r.t_admit = self.clock() - t0
+                active.append([r, lat, 0, [], [], fp])
+                used += fp
+            if not active:
+                if pending[0].arrival <= now:
+                    raise RuntimeError(f"request {pending[0].rid} does not fit the memory budget")
+                time.sleep(min(pending[0].arrival - now, 0.05))
+                continue
+            ids = tuple(id(a[1]) for a in active)
+            if ids != members:
+                if batch is not None:
+                    batch.close()
+                batch = sun.Batch([a[1] for a in active], use_graphs=self.use_graphs)
+                members = ids
+            k = min(self.k, min(a[0].n_sweeps - a[2] for a in active))
+            plaq, poly = batch.run(k, 1, self.n_or)
+            self.ticks += 1
+            for j, a in enumerate(active):
+                a[2] += k
+                a[3].extend(plaq[:, j].tolist())
+                a[4].extend(poly[:, j].tolist())
+                self.link_updates += k * (1 + self.n_or) * 4 * int(np.prod(a[0].dims))
+            done = [a for a in active if a[2] >= a[0].n_sweeps]
+            if done:
+                t = self.clock() - t0
+                for a in done:
+                    r = a[0]
+                    r.t_done = t
+                    r.plaquette = np.array(a[3])
+                    r.polyakov = np.array(a[4])
+                    used -= a[5]
+                active = [a for a in active if a[2] < a[0].n_sweeps]
+                batch.close()
+                batch = None
+                members = None
+                for a in done:
+                    a[1].close()
+                torch.cuda.empty_cache()
+        if batch is not None:
+            batch.close()
+        self.wall = self.clock() - t0
+        return reqs
+
+
+def serve_plain(trace: List[Request], n_overrelax=4, precision=32, clock=time.perf_counter):
+    """One request at a time, in arrival order, each chain alone (sun_run)."""
+    import torch
+
+    reqs = _clone(trace)
+    t0 = clock()
+    updates = 0
+    for r in sorted(reqs, key=lambda q: q.arrival):
+        now = clock() - t0
+        if r.arrival > now:
+            time.sleep(r.arrival - now)
+        r.t_admit = clock() - t0
+        with sun.Lattice(r.nc, r.dims, r.beta, hot_start=True, seed=r.seed, precision=precision) as lat:
+            plaq, poly = lat.run(r.n_sweeps, 1, n_overrelax)
+        r.t_done = clock() - t0
+        r.plaquette, r.polyakov = plaq, poly
+        updates += r.n_sweeps * (1 + n_overrelax) * 4 * int(np.prod(r.dims))
+        torch.cuda.empty_cache()
+    return reqs, clock() - t0, updates
+
+
+def latency_stats(reqs):
+    lat = np.array([r.latency for r in reqs if r.latency is not None])
+    return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(lat.mean()), "max_s": float(lat.max()), "completed": int(len(lat))}

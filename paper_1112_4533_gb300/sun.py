@@ -70,6 +70,9 @@ SIGNATURES = [
     ("sun_synchronize", ctypes.c_int, [_P]),
     ("sun_get_info", ctypes.c_int, [_P, ctypes.POINTER(LatticeInfo)]),
     ("sun_plaquette_noalloc", ctypes.c_int, [_P, ctypes.c_int, _I4, ctypes.c_int, ctypes.c_int, _D, _P]),
+    ("sun_batch_create", ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int, _P, ctypes.c_int]),
+    ("sun_batch_run", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D]),
+    ("sun_batch_destroy", None, [_P]),
 ]
 
 
@@ -280,3 +283,49 @@ class Lattice:
 def lattice_create(nc, dims, beta, hot_start=False, seed=1, **kw):
     """Same as sun_lattice_create: returns a Lattice."""
     return Lattice(nc, dims, beta, hot_start=hot_start, seed=seed, **kw)
+
+
+class Batch:
+    """Independent lattices swept together (sun_batch_*): one kernel launch per
+    pass for all chains of equal (Nc, storage, precision), groups overlapping on
+    their own streams.  The lattices must stay open while the batch lives."""
+
+    def __init__(self, lattices, stream=None, use_graphs=True):
+        self._lib = load_library()
+        self.lattices = list(lattices)
+        arr = (ctypes.c_void_p * len(self.lattices))(*[L.handle.value for L in self.lattices])
+        h = ctypes.c_void_p()
+        s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+        _check(self._lib.sun_batch_create(ctypes.byref(h), arr, len(self.lattices), s, 1 if use_graphs else 0))
+        self._h = h
+
+    @property
+    def n(self):
+        return len(self.lattices)
+
+    def run(self, n_sweeps, n_heatbath=1, n_overrelax=4, plaquette=True, polyakov=True):
+        """Returns (plaquette [n_sweeps, n], Polyakov [n_sweeps, n] complex), None if not asked."""
+        ns, n = int(n_sweeps), self.n
+        ph = np.zeros((ns, n)) if plaquette else None
+        lh = np.zeros((ns, n, 2)) if polyakov else None
+        _check(self._lib.sun_batch_run(self._h, ns, int(n_heatbath), int(n_overrelax),
+                                       _dptr(ph) if ph is not None else None,
+                                       _dptr(lh) if lh is not None else None))
+        return ph, (lh[..., 0] + 1j * lh[..., 1] if lh is not None else None)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.sun_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,102 @@
+"""GPU tests of batches (sun_batch_*): many independent chains of mixed Nc,
+extent, beta and seed swept by shared kernel launches.  A chain in a batch must
+evolve exactly as it does alone (bitwise links: the same per-link kernels, its
+own seed and heatbath counter), its observables must agree to rounding, and a
+batch must match the oracle."""
+import numpy as np
+import pytest
+
+import oracle as orc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sunlib():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1112_4533_gb300 import build as b
+    b.build()
+    import paper_1112_4533_gb300 as p
+    p.load_library()
+    return p
+
+
+# (nc, dims, beta, seed, storage, precision)
+MIX = [
+    (3, (4, 4, 4, 4), 5.7, 11, 12, 32),
+    (3, (6, 6, 6, 6), 6.1, 12, 12, 32),
+    (3, (8, 4, 6, 4), 6.3, 13, 12, 32),
+    (2, (8, 8, 8, 8), 2.3, 14, 4, 32),
+    (4, (4, 4, 4, 6), 11.0, 15, 32, 32),
+    (3, (4, 6, 4, 8), 5.9, 16, 12, 32),
+    (6, (4, 4, 4, 4), 25.0, 17, 72, 32),
+]
+
+
+def make(p, spec, **kw):
+    nc, dims, beta, seed, st, prec = spec
+    return p.Lattice(nc, dims, beta, hot_start=True, seed=seed, storage=st, precision=prec, **kw)
+
+
+@pytest.mark.parametrize("reunit_mode", [0, 1])
+def test_each_chain_in_a_mixed_batch_evolves_as_alone(sunlib, reunit_mode):
+    sweeps = 3
+    alone = []
+    for spec in MIX:
+        with make(sunlib, spec, reunit_mode=reunit_mode) as L:
+            plaq, poly = L.run(sweeps, 1, 2)
+            alone.append((L.export_links(), plaq, poly, L.heatbath_step))
+    lats = [make(sunlib, spec, reunit_mode=reunit_mode) for spec in MIX]
+    with sunlib.Batch(lats) as B:
+        plaq, poly = B.run(sweeps, 1, 2)
+    assert plaq.shape == (sweeps, len(MIX)) and poly.shape == (sweeps, len(MIX))
+    for i, L in enumerate(lats):
+        U, p1, l1, step = alone[i]
+        assert np.array_equal(L.export_links(), U), i
+        assert np.abs(plaq[:, i] - p1).max() < 1e-12, i
+        assert np.abs(poly[:, i] - l1).max() < 1e-12, i
+        assert L.heatbath_step == step == sweeps
+        L.close()
+
+
+def test_batch_graph_replay_equals_direct_launches(sunlib):
+    out = []
+    for graphs in (True, False):
+        lats = [make(sunlib, spec) for spec in MIX[:4]]
+        with sunlib.Batch(lats, use_graphs=graphs) as B:
+            plaq, poly = B.run(4, 1, 3)
+        out.append((plaq, poly, [L.export_links() for L in lats]))
+        for L in lats:
+            L.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    for a, b in zip(out[0][2], out[1][2]):
+        assert np.array_equal(a, b)
+
+
+def test_fp64_batch_matches_oracle(sunlib):
+    specs = [(2, (4, 4, 4, 6), 2.3, 21, 4, 64), (3, (4, 6, 4, 4), 6.0, 22, 18, 64)]
+    lats = [make(sunlib, s) for s in specs]
+    starts = [L.export_links() for L in lats]
+    with sunlib.Batch(lats) as B:
+        plaq, _ = B.run(1, 1, 1)
+    for i, (L, s) in enumerate(zip(lats, specs)):
+        want = starts[i].copy()
+        orc.sweep(want, s[2], 1, 1, True, s[3], 0)
+        assert np.abs(L.export_links() - want).max() < 1e-10
+        assert abs(plaq[0, i] - orc.plaquette(want)) < 1e-10
+        L.close()
+
+
+def test_batch_argument_errors(sunlib):
+    a = make(sunlib, MIX[0])
+    b = make(sunlib, MIX[1], reunit_mode=1)
+    with pytest.raises(sunlib.SunError):
+        sunlib.Batch([a, a])
+    with pytest.raises(sunlib.SunError):
+        sunlib.Batch([a, b])
+    c = make(sunlib, MIX[2], reunit_every=2)
+    with pytest.raises(sunlib.SunError):
+        sunlib.Batch([c])
+    for L in (a, b, c):
+        L.close()
