@@ -458,7 +458,7 @@ def serving_arm(args):
     budget = int(args.budget_gb * (1 << 30))
     warm = serve.poisson_trace(4, rate=50.0, seed=99, Ls=(8,), sweeps=(2, 3))
     serve.Server(budget).run(warm)  # load kernels
-    srv = serve.Server(budget, sweeps_per_tick=args.sweeps_per_tick)
+    srv = serve.Server(budget, sweeps_per_tick=args.sweeps_per_tick, work_cap_ms=args.work_cap_ms)
     t0 = time.perf_counter()
     out = srv.run(trace)
     wall = time.perf_counter() - t0
@@ -471,7 +471,8 @@ def serving_arm(args):
            "dtype": "f32", "data": "synthetic Poisson trace (seed 7)",
            "config": {"workload": f"{args.requests} requests, Poisson mean 20/s, Nc in {{2,3,4,6}}, L in "
                                   "{8,12,16,20,24}, 20..200 sweeps of 1 heatbath + 4 overrelaxation, FP32",
-                      "hbm_budget_gb": args.budget_gb, "sweeps_per_tick": args.sweeps_per_tick},
+                      "hbm_budget_gb": args.budget_gb, "sweeps_per_tick": args.sweeps_per_tick,
+                      "work_cap_ms": args.work_cap_ms},
            "p99_s": st["p99_s"], "mean_s": st["mean_s"], "completed": st["completed"],
            "throughput": {"requests_per_s": len(trace) / wall, "link_updates_per_s": upd / wall},
            "plain": {"p50_s": pst["p50_s"], "p99_s": pst["p99_s"], "mean_s": pst["mean_s"],
@@ -524,7 +525,8 @@ def main():
     ap.add_argument("--workload", choices=["single", "batched", "serving"], default="single")
     ap.add_argument("--requests", type=int, default=80)
     ap.add_argument("--budget-gb", type=float, default=64.0)
-    ap.add_argument("--sweeps-per-tick", type=int, default=2)
+    ap.add_argument("--sweeps-per-tick", type=int, default=8)
+    ap.add_argument("--work-cap-ms", type=float, default=3.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

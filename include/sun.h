@@ -73,13 +73,17 @@ enum { SUN_HEATBATH = 0, SUN_OVERRELAX = 1 };
  *                it must be 256-byte aligned and outlive the lattice.  NULL = the
  *                library allocates (cudaMalloc) and frees.
  *  use_graphs    sun_run captures one sweep as a CUDA graph and replays it (default 1).
- *  variant       update-pass kernel variant, bit flags (default 0), built for SU(3)
- *                FP32 and ignored elsewhere: 1 = bound the registers for 6
- *                resident 128-thread blocks per SM (same results); 2 = with
- *                two-row storage, multiply out rows 0 and 1 of each staple term
- *                only and take its third row as conj(row0 x row1), exact for SU(3)
- *                products (results move by the order of the links' unitarity
- *                drift, ~1e-6 between re-unitarizations).
+ *  variant       update-pass kernel variant, bit flags (default 0); results do not
+ *                depend on bits 1 and 4:
+ *                1 = (SU(3) FP32) bound the registers for 6 resident 128-thread
+ *                blocks per SM;
+ *                2 = (SU(3) FP32 two-row storage) multiply out rows 0 and 1 of each
+ *                staple term only and take its third row as conj(row0 x row1),
+ *                exact for SU(3) products (results move by the order of the
+ *                links' unitarity drift, ~1e-6 between re-unitarizations);
+ *                4 = (Nc = 4, 6) swap the pass kernel: by default Nc = 6 runs the
+ *                row-parallel kernel (Nc threads per link) and Nc = 4 one thread
+ *                per link.
  *  reunit_mode   where a sweep re-unitarizes (default 0); every link is
  *                re-unitarized once per re-unitarizing sweep in all three:
  *                0 = all links after the sweep's last step, as a pass of its own

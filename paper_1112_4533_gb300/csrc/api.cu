@@ -147,7 +147,7 @@ struct sun_lattice {
   double* results = nullptr;
   double* hist = nullptr;
   double* staging = nullptr;
-  double* host_results = nullptr;  // pinned, 8 doubles
+  double host_results[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // pageable: creating a lattice pins nothing
   std::map<GraphKey, cudaGraphExec_t> graphs;
 };
 
@@ -293,7 +293,7 @@ static sun_status resolve(int nc, const int* dims, const sun_options* opt_in, su
   if (opt->storage == 0) opt->storage = default_storage(nc);
   if (opt->reunit_every < 0) return fail(SUN_ERR_ARG, "reunit_every must be >= 0");
   if (opt->block_threads == 0) opt->block_threads = 128;
-  if (opt->variant < 0 || opt->variant > 3) return fail(SUN_ERR_ARG, "variant = %d must be in 0..3", opt->variant);
+  if (opt->variant < 0 || opt->variant > 7) return fail(SUN_ERR_ARG, "variant = %d must be in 0..7", opt->variant);
   if (opt->reunit_mode < 0 || opt->reunit_mode > 2)
     return fail(SUN_ERR_ARG, "reunit_mode = %d must be 0, 1 or 2", opt->reunit_mode);
   if (opt->block_threads < 32 || opt->block_threads > 256 || (opt->block_threads & 31))
@@ -371,8 +371,6 @@ sun_status sun_lattice_create(sun_lattice** out, int nc, const int dims[4], doub
   }
   if (cudaStreamCreateWithFlags(&L->capture_stream, cudaStreamNonBlocking) != cudaSuccess)
     return cleanup(fail(SUN_ERR_CUDA, "capture stream creation failed"));
-  if (cudaMallocHost(&L->host_results, 8 * sizeof(double)) != cudaSuccess)
-    return cleanup(fail(SUN_ERR_CUDA, "pinned result buffer allocation failed"));
 
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, L->device);
@@ -405,6 +403,8 @@ sun_status sun_lattice_create(sun_lattice** out, int nc, const int dims[4], doub
   c.stream = L->stream;
   c.block_threads = L->block_threads;
   c.variant = opt.variant;
+  c.obs_stride = 1;
+  c.obs_offset = 0;
   int rb = 2 * (sms > 0 ? sms : 132);
   c.reduce_blocks = rb > sun::kMaxReduceBlocks ? sun::kMaxReduceBlocks : rb;
   L->results = reinterpret_cast<double*>(L->base + L->plan.results_off);
@@ -427,7 +427,6 @@ void sun_lattice_destroy(sun_lattice* L) {
   if (L->capture_stream) cudaStreamDestroy(L->capture_stream);
   if (L->own_stream && L->stream) cudaStreamDestroy(L->stream);
   if (L->own_mem && L->base) cudaFree(L->base);
-  if (L->host_results) cudaFreeHost(L->host_results);
   delete L;
 }
 
@@ -636,11 +635,12 @@ __global__ void slot_bump_kernel(uint32_t* slot) { *slot += 1u; }
 
 struct BatchGroup {
   const sun::Ops* ops = nullptr;
-  std::vector<sun_lattice*> members;
+  std::vector<sun_lattice*> members;  // chains packed into shared launches, then the large chains
+  int n_small = 0;                    // members[0, n_small) are packed; the rest run their own launches
   int offset = 0;  // position of the first member in the create call order of the batch table
   std::vector<int> positions;  // create-call position of each member
-  sun::ChainDesc* d_chains = nullptr;
-  uint32_t* d_start = nullptr;  // pass, reunit, plaquette, Polyakov tables, n+1 each
+  sun::ChainDesc* d_chains = nullptr;  // all members (packed ones first)
+  uint32_t* d_start = nullptr;  // pass, reunit, plaquette, Polyakov, row-parallel pass tables, n_small+1 each
   double* d_partials = nullptr;
   int* d_pos = nullptr;
   sun::BatchCtx ctx{};
@@ -661,7 +661,7 @@ struct sun_batch {
   cudaEvent_t fork = nullptr;
   uint32_t* d_slot = nullptr;
   double* d_hist = nullptr;  // [cap][n] plaquette, then [cap][n][2] Polyakov (group-ordered columns)
-  double* h_hist = nullptr;
+  std::vector<double> h_hist;
   int hist_cap = 0;
   int reunit_every = 1, reunit_mode = 0;
   uint64_t sweeps_done = 0;
@@ -671,12 +671,14 @@ struct sun_batch {
 
 namespace {
 
+// batch tables are stream-ordered allocations: creating and destroying a batch
+// (as a server does whenever its set of chains changes) never synchronises the device
 template <class T>
-sun_status dev_alloc(T** p, size_t count) {
+sun_status dev_alloc(T** p, size_t count, cudaStream_t s) {
   void* q = nullptr;
-  if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) {
+  if (cudaMallocAsync(&q, count * sizeof(T), s) != cudaSuccess) {
     cudaGetLastError();
-    return fail(SUN_ERR_OOM, "cudaMalloc of %zu bytes for a batch table failed", count * sizeof(T));
+    return fail(SUN_ERR_OOM, "cudaMallocAsync of %zu bytes for a batch table failed", count * sizeof(T));
   }
   *p = static_cast<T*>(q);
   return SUN_OK;
@@ -700,21 +702,35 @@ sun_status enqueue_batch_sweep(sun_batch* B, cudaStream_t s, int n_hb, int n_or,
         rem = uint32_t(step);
       }
       for (int mu = 0; mu < 4; ++mu)
-        for (int p = 0; p < 2; ++p)
-          SUN_TRY(check_launch(g.ops->batch_pass(c, hb ? SUN_HEATBATH : SUN_OVERRELAX, mu, p, hb ? uint32_t(step) : 0u,
-                                                 mod, rem),
-                               "batched pass"));
+        for (int p = 0; p < 2; ++p) {
+          const int mode = hb ? SUN_HEATBATH : SUN_OVERRELAX;
+          const uint32_t so = hb ? uint32_t(step) : 0u;
+          if (g.n_small > 0) SUN_TRY(check_launch(g.ops->batch_pass(c, mode, mu, p, so, mod, rem), "batched pass"));
+          for (size_t k = size_t(g.n_small); k < g.members.size(); ++k)
+            SUN_TRY(check_launch(g.ops->pass(ctx_on(g.members[k], g.stream), mode, mu, p, so, mod, rem), "pass"));
+        }
     }
-    if (reunit && !fused) SUN_TRY(check_launch(g.ops->batch_reunit(c), "batched reunitarization"));
     const uint32_t* slot = hist_mode ? B->d_slot : nullptr;
-    if (plaq) SUN_TRY(check_launch(g.ops->batch_plaquette(c, B->d_hist, slot, B->hist_cap, g.offset, B->n),
-                                   "batched plaquette"));
-    if (poly)
-      SUN_TRY(check_launch(g.ops->batch_polyakov(c, B->d_hist + size_t(B->hist_cap) * B->n, slot, B->hist_cap,
-                                                 g.offset, B->n),
-                           "batched polyakov"));
+    double* hist_p = B->d_hist;
+    double* hist_l = B->d_hist + size_t(B->hist_cap) * B->n;
+    if (g.n_small > 0) {
+      if (reunit && !fused) SUN_TRY(check_launch(g.ops->batch_reunit(c), "batched reunitarization"));
+      if (plaq) SUN_TRY(check_launch(g.ops->batch_plaquette(c, hist_p, slot, B->hist_cap, g.offset, B->n),
+                                     "batched plaquette"));
+      if (poly) SUN_TRY(check_launch(g.ops->batch_polyakov(c, hist_l, slot, B->hist_cap, g.offset, B->n),
+                                     "batched polyakov"));
+    }
+    for (size_t k = size_t(g.n_small); k < g.members.size(); ++k) {
+      sun::Ctx lc = ctx_on(g.members[k], g.stream);
+      lc.obs_stride = B->n;
+      lc.obs_offset = g.offset + int(k);
+      if (reunit && !fused) SUN_TRY(check_launch(g.ops->reunit(lc), "reunitarization"));
+      if (plaq) SUN_TRY(check_launch(g.ops->plaquette(lc, hist_p, slot, B->hist_cap), "plaquette"));
+      if (poly) SUN_TRY(check_launch(g.ops->polyakov(lc, hist_l, slot, B->hist_cap), "polyakov"));
+    }
     if (n_hb > 0) {
-      batch_bump_kernel<<<unsigned((g.ctx.n + 127) / 128), 128, 0, g.stream>>>(g.d_chains, g.ctx.n, uint32_t(n_hb));
+      const int all = int(g.members.size());
+      batch_bump_kernel<<<unsigned((all + 127) / 128), 128, 0, g.stream>>>(g.d_chains, all, uint32_t(n_hb));
       SUN_TRY(check_launch(cudaGetLastError(), "batched step counter"));
     }
     SUN_CUDA(cudaEventRecord(g.done, g.stream));
@@ -786,19 +802,42 @@ sun_status sun_batch_create(sun_batch** out, sun_lattice* const* lattices, int n
   B->reunit_mode = L0->reunit_mode;
   B->use_graphs = use_graphs;
   if (cudaSetDevice(B->device) != cudaSuccess) return cleanup(fail(SUN_ERR_CUDA, "cudaSetDevice failed"));
-
-  // groups in order of first appearance; members in create-call order
-  for (int i = 0; i < n; ++i) {
-    sun_lattice* L = lattices[i];
-    auto it = std::find_if(B->groups.begin(), B->groups.end(), [&](const BatchGroup& g) { return g.ops == L->ops; });
-    if (it == B->groups.end()) {
-      B->groups.emplace_back();
-      it = B->groups.end() - 1;
-      it->ops = L->ops;
-    }
-    it->members.push_back(L);
-    it->positions.push_back(i);
+  if (stream) {
+    B->stream = static_cast<cudaStream_t>(stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking) != cudaSuccess)
+      return cleanup(fail(SUN_ERR_CUDA, "stream creation failed"));
+    B->own_stream = true;
   }
+
+  // groups in order of first appearance; in a group the chains packed into shared
+  // launches come first (create-call order), then the Nc >= 4 chains that fill
+  // the GPU on their own (at least 4 blocks per SM per pass), which run the
+  // single-lattice kernels inside the batch (their packed kernels are slower)
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, B->device);
+  if (sms <= 0) sms = 132;
+  auto is_large = [&](const sun_lattice* L) {
+    if (L->nc < 4) return false;  // Nc <= 3: the packed kernels run as fast as the single-lattice ones
+    const int lpb = L->ops->group_links_per_block > 0 && !(L->ctx.variant & 4) && L->nc == 6
+                        ? L->ops->group_links_per_block
+                        : ((L->ctx.variant & 1) ? 128 : L->block_threads);
+    return L->ctx.g.Vh >= int64_t(4) * sms * lpb;
+  };
+  for (int pass = 0; pass < 2; ++pass)
+    for (int i = 0; i < n; ++i) {
+      sun_lattice* L = lattices[i];
+      if (is_large(L) != (pass == 1)) continue;
+      auto it = std::find_if(B->groups.begin(), B->groups.end(), [&](const BatchGroup& g) { return g.ops == L->ops; });
+      if (it == B->groups.end()) {
+        B->groups.emplace_back();
+        it = B->groups.end() - 1;
+        it->ops = L->ops;
+      }
+      it->members.push_back(L);
+      it->positions.push_back(i);
+      if (pass == 0) it->n_small++;
+    }
   // history columns are group-ordered: column offset of each group
   int col = 0;
   for (auto& g : B->groups) {
@@ -806,13 +845,15 @@ sun_status sun_batch_create(sun_batch** out, sun_lattice* const* lattices, int n
     col += int(g.members.size());
   }
   for (auto& g : B->groups) {
-    const int m = int(g.members.size());
+    const int all = int(g.members.size());
+    const int m = g.n_small;  // the tables cover the packed chains
     const sun_lattice* first = g.members[0];
     const int bt = (first->ctx.variant & 1) ? 128 : first->block_threads;
-    std::vector<sun::ChainDesc> desc(m);
-    std::vector<uint32_t> start(4 * (m + 1), 0);
-    uint64_t tot[4] = {0, 0, 0, 0};
-    for (int k = 0; k < m; ++k) {
+    std::vector<sun::ChainDesc> desc(all);
+    std::vector<uint32_t> start(5 * (m + 1), 0);
+    uint64_t tot[5] = {0, 0, 0, 0, 0};
+    const int glpb = g.ops->group_links_per_block > 0 ? g.ops->group_links_per_block : 1;
+    for (int k = 0; k < all; ++k) {
       const sun_lattice* L = g.members[k];
       const sun::Geom& ge = L->ctx.g;
       sun::ChainDesc& d = desc[k];
@@ -825,24 +866,29 @@ sun_status sun_batch_create(sun_batch** out, sun_lattice* const* lattices, int n
       const int64_t nsp = int64_t(ge.nx) * ge.ny * ge.nz;
       d.plaq_scale = 1.0 / (6.0 * double(ge.V) * L->nc);
       d.poly_scale = 1.0 / (double(L->nc) * double(nsp));
-      const uint64_t blocks[4] = {uint64_t((ge.Vh + bt - 1) / bt), uint64_t((8 * ge.Vh + 127) / 128),
-                                  uint64_t((ge.V + 255) / 256), uint64_t((nsp + 127) / 128)};
-      for (int q = 0; q < 4; ++q) {
+      const uint64_t blocks[5] = {uint64_t((ge.Vh + bt - 1) / bt), uint64_t((8 * ge.Vh + 127) / 128),
+                                  uint64_t((ge.V + 255) / 256), uint64_t((nsp + 127) / 128),
+                                  uint64_t((ge.Vh + glpb - 1) / glpb)};
+      if (k >= m) continue;
+      for (int q = 0; q < 5; ++q) {
         start[q * (m + 1) + k] = uint32_t(tot[q]);
         tot[q] += blocks[q];
       }
     }
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < 5; ++q) {
       if (tot[q] >= (uint64_t(1) << 31)) return cleanup(fail(SUN_ERR_ARG, "batch too large for one grid"));
       start[q * (m + 1) + m] = uint32_t(tot[q]);
     }
     sun_status st;
-    if ((st = dev_alloc(&g.d_chains, size_t(m))) != SUN_OK) return cleanup(st);
-    if ((st = dev_alloc(&g.d_start, start.size())) != SUN_OK) return cleanup(st);
-    const size_t npart = std::max<size_t>(tot[2], 2 * tot[3]);
-    if ((st = dev_alloc(&g.d_partials, npart)) != SUN_OK) return cleanup(st);
-    if (cudaMemcpy(g.d_chains, desc.data(), m * sizeof(sun::ChainDesc), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(g.d_start, start.data(), start.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess)
+    if ((st = dev_alloc(&g.d_chains, size_t(all), B->stream)) != SUN_OK) return cleanup(st);
+    if ((st = dev_alloc(&g.d_start, start.size(), B->stream)) != SUN_OK) return cleanup(st);
+    const size_t npart = std::max<size_t>({size_t(1), size_t(tot[2]), size_t(2 * tot[3])});
+    if ((st = dev_alloc(&g.d_partials, npart, B->stream)) != SUN_OK) return cleanup(st);
+    // pageable sources: the copies return once the tables are staged
+    if (cudaMemcpyAsync(g.d_chains, desc.data(), all * sizeof(sun::ChainDesc), cudaMemcpyHostToDevice, B->stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(g.d_start, start.data(), start.size() * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                        B->stream) != cudaSuccess)
       return cleanup(fail(SUN_ERR_CUDA, "upload of a batch table failed"));
     if (cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming) != cudaSuccess)
@@ -854,6 +900,8 @@ sun_status sun_batch_create(sun_batch** out, sun_lattice* const* lattices, int n
     c.reunit_start = g.d_start + (m + 1);
     c.plaq_start = g.d_start + 2 * (m + 1);
     c.poly_start = g.d_start + 3 * (m + 1);
+    c.group_start = g.d_start + 4 * (m + 1);
+    c.group_blocks = uint32_t(tot[4]);
     c.pass_blocks = uint32_t(tot[0]);
     c.reunit_blocks = uint32_t(tot[1]);
     c.plaq_blocks = uint32_t(tot[2]);
@@ -862,22 +910,14 @@ sun_status sun_batch_create(sun_batch** out, sun_lattice* const* lattices, int n
     c.variant = first->ctx.variant;
     c.partials = g.d_partials;
   }
-  if (stream) {
-    B->stream = static_cast<cudaStream_t>(stream);
-  } else {
-    if (cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking) != cudaSuccess)
-      return cleanup(fail(SUN_ERR_CUDA, "stream creation failed"));
-    B->own_stream = true;
-  }
   if (cudaStreamCreateWithFlags(&B->capture_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming) != cudaSuccess)
     return cleanup(fail(SUN_ERR_CUDA, "batch stream creation failed"));
   B->hist_cap = int(std::max<int64_t>(1, std::min<int64_t>(kHistCap, (int64_t(4) << 20) / (3 * int64_t(n)))));
   sun_status st;
-  if ((st = dev_alloc(&B->d_slot, 1)) != SUN_OK) return cleanup(st);
-  if ((st = dev_alloc(&B->d_hist, size_t(3) * B->hist_cap * n)) != SUN_OK) return cleanup(st);
-  if (cudaMallocHost(&B->h_hist, size_t(3) * B->hist_cap * n * sizeof(double)) != cudaSuccess)
-    return cleanup(fail(SUN_ERR_CUDA, "pinned history buffer allocation failed"));
+  if ((st = dev_alloc(&B->d_slot, 1, B->stream)) != SUN_OK) return cleanup(st);
+  if ((st = dev_alloc(&B->d_hist, size_t(3) * B->hist_cap * n, B->stream)) != SUN_OK) return cleanup(st);
+  B->h_hist.assign(size_t(3) * B->hist_cap * n, 0.0);
   *out = B;
   return SUN_OK;
 }
@@ -885,24 +925,31 @@ sun_status sun_batch_create(sun_batch** out, sun_lattice* const* lattices, int n
 void sun_batch_destroy(sun_batch* B) {
   if (!B) return;
   cudaSetDevice(B->device);
-  if (B->stream) cudaStreamSynchronize(B->stream);
   for (auto& kv : B->graphs) cudaGraphExecDestroy(kv.second);
   for (auto& g : B->groups) {
     if (g.stream) {
-      cudaStreamSynchronize(g.stream);
-      cudaStreamDestroy(g.stream);
+      // the batch stream frees the tables after the group's last work
+      if (g.done && B->stream) {
+        cudaEventRecord(g.done, g.stream);
+        cudaStreamWaitEvent(B->stream, g.done, 0);
+      }
     }
+    if (B->stream) {
+      if (g.d_chains) cudaFreeAsync(g.d_chains, B->stream);
+      if (g.d_start) cudaFreeAsync(g.d_start, B->stream);
+      if (g.d_partials) cudaFreeAsync(g.d_partials, B->stream);
+    }
+    if (g.stream) cudaStreamDestroy(g.stream);
     if (g.done) cudaEventDestroy(g.done);
-    cudaFree(g.d_chains);
-    cudaFree(g.d_start);
-    cudaFree(g.d_partials);
+  }
+  if (B->stream) {
+    if (B->d_slot) cudaFreeAsync(B->d_slot, B->stream);
+    if (B->d_hist) cudaFreeAsync(B->d_hist, B->stream);
   }
   if (B->fork) cudaEventDestroy(B->fork);
   if (B->capture_stream) cudaStreamDestroy(B->capture_stream);
+  if (B->stream) cudaStreamSynchronize(B->stream);
   if (B->own_stream && B->stream) cudaStreamDestroy(B->stream);
-  cudaFree(B->d_slot);
-  cudaFree(B->d_hist);
-  if (B->h_hist) cudaFreeHost(B->h_hist);
   delete B;
 }
 
@@ -927,7 +974,7 @@ sun_status sun_batch_run(sun_batch* B, int n_sweeps, int n_hb, int n_or, double*
       }
     }
     if (want_p || want_l) {
-      SUN_CUDA(cudaMemcpyAsync(B->h_hist, B->d_hist, size_t(3) * B->hist_cap * n * sizeof(double),
+      SUN_CUDA(cudaMemcpyAsync(B->h_hist.data(), B->d_hist, size_t(3) * B->hist_cap * n * sizeof(double),
                                cudaMemcpyDeviceToHost, B->stream));
       SUN_CUDA(cudaStreamSynchronize(B->stream));
       // group-ordered columns back to create-call order
@@ -937,7 +984,7 @@ sun_status sun_batch_run(sun_batch* B, int n_sweeps, int n_hb, int n_or, double*
           for (int r = 0; r < chunk; ++r) {
             if (want_p) plaq[size_t(done + r) * n + pos] = B->h_hist[size_t(r) * n + colg];
             if (want_l) {
-              const double* src = B->h_hist + size_t(B->hist_cap) * n + (size_t(r) * n + colg) * 2;
+              const double* src = B->h_hist.data() + size_t(B->hist_cap) * n + (size_t(r) * n + colg) * 2;
               poly[(size_t(done + r) * n + pos) * 2] = src[0];
               poly[(size_t(done + r) * n + pos) * 2 + 1] = src[1];
             }

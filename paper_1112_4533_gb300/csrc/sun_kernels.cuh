@@ -398,6 +398,333 @@ __global__ void __launch_bounds__(128, 6) update_pass_mat_occ(const PassParams p
   pass_body<R, N, S, MODE, (VAR & 2) != 0, REUNIT>(p, h);
 }
 
+// ---------------------------------------------------------------------------
+// Row-parallel pass for SU(Nc), Nc = 4 and 6 (no fused re-unitarization):
+// Nc threads of a warp share one link.  Thread r owns row r of the staple and
+// of U, the neighbour links of each staple term are staged row by row in
+// shared memory, and for the SU(2) subgroup updates (Eq. 15) thread c owns
+// column c of U and W, so every lane works on every subgroup.  The heatbath
+// draw runs Nc attempts at once, one per lane; the first accepted attempt in
+// attempt order is taken (warp ballot), so the random stream and the result are
+// those of the one-attempt-at-a-time sampler.  Lanes beyond the last whole
+// group of a warp run a copy of a real link and never store.
+// ---------------------------------------------------------------------------
+template <class R, int N>
+struct Group {
+  static constexpr int LPW = 32 / N;          // links per warp
+  static constexpr int WARPS = 4;             // warps per block (128 threads)
+  static constexpr int LPB = WARPS * LPW;     // links per block
+  static constexpr int SLOTS = (32 + N - 1) / N;  // link slots per warp in shared memory
+  static constexpr int CPR = 2 * N * int(sizeof(R)) / 16;  // 16-byte components per row
+};
+
+template <class R, int N>
+constexpr bool has_group() {
+  return (N == 4 || N == 6) && (2 * N * int(sizeof(R))) % 16 == 0;
+}
+
+// Default choice between the row-parallel and the one-thread-per-link pass
+// (measured on 24^4: row-parallel is faster for Nc = 6, slower for Nc = 4 whose
+// matrices fit in registers); kernel variant bit 4 takes the other one.
+template <class R, int N>
+__host__ __device__ constexpr bool group_by_default() {
+  return N == 6;
+}
+
+template <class R, int N>
+__host__ __device__ inline bool use_group(int variant) {
+  return has_group<R, N>() && (group_by_default<R, N>() != ((variant & 4) != 0));
+}
+
+// row r of a full-storage link
+template <class R, int N>
+__device__ __forceinline__ void load_row(const char* blk, int64_t Vh, int64_t h, int r, Cpx<R> (&row)[N]) {
+  using V = typename Vec16<R>::T;
+  constexpr int per16 = 16 / int(sizeof(R));
+  R buf[2 * N];
+#pragma unroll
+  for (int c = 0; c < Group<R, N>::CPR; ++c) {
+    const V* p = reinterpret_cast<const V*>(blk + (int64_t(r * Group<R, N>::CPR + c) * Vh + h) * 16);
+    unpack(__ldg(p), &buf[c * per16]);
+  }
+#pragma unroll
+  for (int k = 0; k < N; ++k) row[k] = {buf[2 * k], buf[2 * k + 1]};
+}
+
+template <class R, int N>
+__device__ __forceinline__ void load_row_rw(const char* blk, int64_t Vh, int64_t h, int r, Cpx<R> (&row)[N]) {
+  using V = typename Vec16<R>::T;
+  constexpr int per16 = 16 / int(sizeof(R));
+  R buf[2 * N];
+#pragma unroll
+  for (int c = 0; c < Group<R, N>::CPR; ++c) {
+    const V* p = reinterpret_cast<const V*>(blk + (int64_t(r * Group<R, N>::CPR + c) * Vh + h) * 16);
+    unpack(*p, &buf[c * per16]);
+  }
+#pragma unroll
+  for (int k = 0; k < N; ++k) row[k] = {buf[2 * k], buf[2 * k + 1]};
+}
+
+template <class R, int N>
+__device__ __forceinline__ void store_row(char* blk, int64_t Vh, int64_t h, int r, const Cpx<R> (&row)[N]) {
+  using V = typename Vec16<R>::T;
+  constexpr int per16 = 16 / int(sizeof(R));
+  R buf[2 * N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    buf[2 * k] = row[k].re;
+    buf[2 * k + 1] = row[k].im;
+  }
+#pragma unroll
+  for (int c = 0; c < Group<R, N>::CPR; ++c) {
+    V* p = reinterpret_cast<V*>(blk + (int64_t(r * Group<R, N>::CPR + c) * Vh + h) * 16);
+    *p = pack4(&buf[c * per16]);
+  }
+}
+
+template <class R, int N>
+__device__ __forceinline__ void smem_put_row(Cpx<R> (*m)[N], int r, const Cpx<R> (&row)[N]) {
+#pragma unroll
+  for (int k = 0; k < N; ++k) m[r][k] = row[k];
+}
+
+// heatbath element of one subgroup drawn by the Nc lanes of a group at once
+template <class R, int N>
+__device__ __forceinline__ bool heatbath_su2_group(R alpha, bool skip, uint2 key, uint32_t link, uint32_t step,
+                                                   uint32_t sub, int r, int base, Quat<R>& b) {
+  const bool kp = alpha >= R(1.5);
+  const R inv2a = R(1) / (R(2) * alpha);
+  const R e = -d_expm1(R(-2) * alpha);
+  bool found = skip;
+  bool got = false;
+  R b0 = R(1);
+  for (int round = 0; round * N < kHeatbathAttempts; ++round) {
+    const int att = round * N + r;
+    bool acc = false;
+    R x = R(1);
+    if (!found && att < kHeatbathAttempts) {
+      const uint4 u = philox4x32_10(make_uint4(link, step, (sub << 16) | uint32_t(att), kTagHeatbath), key);
+      const R r0 = u01<R>(u.x), r1 = u01<R>(u.y), r2 = u01<R>(u.z), r3 = u01<R>(u.w);
+      if (kp) {
+        const R c = d_cospi(R(2) * r1);
+        const R delta = -(d_log(r0) + c * c * d_log(r2)) * inv2a;
+        acc = r3 * r3 <= R(1) - delta;
+        x = R(1) - R(2) * delta;
+      } else {
+        x = alpha > R(0) ? R(1) + d_log1p(-r0 * e) / alpha : R(1) - R(2) * r0;
+        acc = r1 * r1 <= R(1) - x * x;
+      }
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, acc);
+    const unsigned mine = (base < 32 ? (bal >> base) : 0u) & ((1u << N) - 1u);
+    const int first = mine ? __ffs(mine) - 1 : 0;
+    const R xb = __shfl_sync(0xffffffffu, x, (base + first) & 31);
+    if (!found && mine) {
+      b0 = xb;
+      found = true;
+      got = true;
+    }
+    if (!__any_sync(0xffffffffu, !found)) break;
+  }
+  if (!got) return false;
+  const uint4 u = philox4x32_10(make_uint4(link, step, (sub << 16) | uint32_t(kHeatbathAttempts), kTagHeatbath), key);
+  const R cth = R(2) * u01<R>(u.x) - R(1);
+  const R sth = d_sqrt(R(1) - cth * cth);
+  R sphi, cphi;
+  d_sincospi(R(2) * u01<R>(u.y), &sphi, &cphi);
+  const R rho = d_sqrt(fmax(R(0), R(1) - b0 * b0));
+  b.a0 = b0;
+  b.a1 = rho * sth * cphi;
+  b.a2 = rho * sth * sphi;
+  b.a3 = rho * cth;
+  return true;
+}
+
+template <class R, int N, int MODE>
+__device__ __forceinline__ void group_pass_body(const PassParams& p, int64_t h, bool active, int r, int base,
+                                                Cpx<R> (*sm)[N][N]) {
+  const Geom& g = p.g;
+  const int mu = p.mu, par = p.parity, opp = par ^ 1;
+  const Site s = decode_half(g, h, par);
+  const uint32_t lex = uint32_t(s.lex);
+  const int cmu = coord_of(s, mu);
+  const uint32_t lex_pmu = fwd(g, lex, cmu, mu);
+
+  Cpx<R> st[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) st[k] = {R(0), R(0)};
+#pragma unroll
+  for (int nu = 0; nu < 4; ++nu) {
+    if (nu == mu) continue;
+    const int cnu = s.c[nu];
+    const uint32_t lex_pnu = fwd(g, lex, cnu, nu);
+    const uint32_t lex_mnu = bwd(g, lex, cnu, nu);
+    const uint32_t lex_mnu_pmu = fwd(g, lex_mnu, cmu, mu);
+    {  // U_nu(x) U_mu(x+nu) U_nu(x+mu)^+ : row r of a, then (a B) C^+
+      Cpx<R> a[N], row[N];
+      load_row<R, N>(block_ptr(p, nu, par), g.Vh, h, r, a);
+      load_row<R, N>(block_ptr(p, mu, opp), g.Vh, lex_pnu >> 1, r, row);
+      smem_put_row<R, N>(sm[0], r, row);
+      load_row<R, N>(block_ptr(p, nu, opp), g.Vh, lex_pmu >> 1, r, row);
+      smem_put_row<R, N>(sm[1], r, row);
+      __syncwarp();
+      Cpx<R> ab[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        Cpx<R> x = cmul(a[0], sm[0][0][j]);
+#pragma unroll
+        for (int k = 1; k < N; ++k) cfma(x, a[k], sm[0][k][j]);
+        ab[j] = x;
+      }
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        Cpx<R> x = cmulc(ab[0], sm[1][j][0]);
+#pragma unroll
+        for (int k = 1; k < N; ++k) cfmac(x, ab[k], sm[1][j][k]);
+        st[j].re += x.re;
+        st[j].im += x.im;
+      }
+      __syncwarp();
+    }
+    {  // U_nu(x-nu)^+ U_mu(x-nu) U_nu(x-nu+mu) : row r of A^+ (B C)
+      Cpx<R> b[N], row[N];
+      load_row<R, N>(block_ptr(p, nu, opp), g.Vh, lex_mnu >> 1, r, row);
+      smem_put_row<R, N>(sm[0], r, row);
+      load_row<R, N>(block_ptr(p, mu, opp), g.Vh, lex_mnu >> 1, r, b);
+      load_row<R, N>(block_ptr(p, nu, par), g.Vh, lex_mnu_pmu >> 1, r, row);
+      smem_put_row<R, N>(sm[1], r, row);
+      __syncwarp();
+      Cpx<R> bc[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        Cpx<R> x = cmul(b[0], sm[1][0][j]);
+#pragma unroll
+        for (int k = 1; k < N; ++k) cfma(x, b[k], sm[1][k][j]);
+        bc[j] = x;
+      }
+      smem_put_row<R, N>(sm[2], r, bc);
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        Cpx<R> x = ccmul(sm[0][0][r], sm[2][0][j]);
+#pragma unroll
+        for (int k = 1; k < N; ++k) ccfma(x, sm[0][k][r], sm[2][k][j]);
+        st[j].re += x.re;
+        st[j].im += x.im;
+      }
+      __syncwarp();
+    }
+  }
+
+  // W = U Sigma^+ (row r), then columns of U and W for the subgroup updates
+  char* ublk = p.links + (2 * mu + par) * p.block_bytes;
+  Cpx<R> u[N], w[N];
+  load_row_rw<R, N>(ublk, g.Vh, h, r, u);
+  smem_put_row<R, N>(sm[0], r, st);
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    Cpx<R> x = cmulc(u[0], sm[0][j][0]);
+#pragma unroll
+    for (int k = 1; k < N; ++k) cfmac(x, u[k], sm[0][j][k]);
+    w[j] = x;
+  }
+  smem_put_row<R, N>(sm[1], r, u);
+  smem_put_row<R, N>(sm[2], r, w);
+  __syncwarp();
+  Cpx<R> uc[N], wc[N];  // column r
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    uc[i] = sm[1][i][r];
+    wc[i] = sm[2][i][r];
+  }
+  __syncwarp();
+
+  uint32_t step = 0;
+  if constexpr (MODE == kHeatbathMode) step = *p.hb_step + p.step_offset;
+  const uint32_t link_id = uint32_t(mu) * uint32_t(g.V) + lex;
+  const R alpha_coef = R(p.alpha_coef);
+  int sub = 0;
+#pragma unroll
+  for (int i = 0; i < N - 1; ++i) {
+#pragma unroll
+    for (int j = i + 1; j < N; ++j) {
+      const bool last = (i == N - 2) && (j == N - 1);
+      // W_ii, W_ji sit in lane i (column i), W_ij, W_jj in lane j (column j)
+      const Cpx<R> wii = {__shfl_sync(0xffffffffu, wc[i].re, (base + i) & 31), __shfl_sync(0xffffffffu, wc[i].im, (base + i) & 31)};
+      const Cpx<R> wji = {__shfl_sync(0xffffffffu, wc[j].re, (base + i) & 31), __shfl_sync(0xffffffffu, wc[j].im, (base + i) & 31)};
+      const Cpx<R> wij = {__shfl_sync(0xffffffffu, wc[i].re, (base + j) & 31), __shfl_sync(0xffffffffu, wc[i].im, (base + j) & 31)};
+      const Cpx<R> wjj = {__shfl_sync(0xffffffffu, wc[j].re, (base + j) & 31), __shfl_sync(0xffffffffu, wc[j].im, (base + j) & 31)};
+      const Quat<R> v = block_to_quat(wii, wij, wji, wjj);
+      const R k = d_sqrt(fma(v.a0, v.a0, fma(v.a1, v.a1, fma(v.a2, v.a2, v.a3 * v.a3))));
+      const bool ok = active && k > R(1e-15) && d_isfinite(k);
+      const R inv = ok ? R(1) / k : R(0);
+      const Quat<R> vd = {v.a0 * inv, -v.a1 * inv, -v.a2 * inv, -v.a3 * inv};
+      Quat<R> a;
+      bool apply = ok;
+      if constexpr (MODE == kHeatbathMode) {
+        Quat<R> b;
+        const bool drawn = heatbath_su2_group<R, N>(ok ? alpha_coef * k : R(1), !ok, p.key, link_id, step,
+                                                    uint32_t(sub), r, base, b);
+        apply = ok && drawn;
+        a = qmul(b, vd);
+      } else {
+        a = qmul(vd, vd);
+      }
+      if (apply) {
+        const Cpx<R> A00 = {a.a0, a.a3}, A01 = {a.a2, a.a1}, A10 = {-a.a2, a.a1}, A11 = {a.a0, -a.a3};
+        Cpx<R> ni = cmul(A00, uc[i]), nj = cmul(A10, uc[i]);
+        cfma(ni, A01, uc[j]);
+        cfma(nj, A11, uc[j]);
+        uc[i] = ni;
+        uc[j] = nj;
+        if (!last) {
+          Cpx<R> mi = cmul(A00, wc[i]), mj = cmul(A10, wc[i]);
+          cfma(mi, A01, wc[j]);
+          cfma(mj, A11, wc[j]);
+          wc[i] = mi;
+          wc[j] = mj;
+        }
+      }
+      ++sub;
+    }
+  }
+  // back to rows and store
+#pragma unroll
+  for (int i = 0; i < N; ++i) sm[0][i][r] = uc[i];
+  __syncwarp();
+  if (active) {
+    Cpx<R> row[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) row[k] = sm[0][r][k];
+    store_row<R, N>(ublk, g.Vh, h, r, row);
+  }
+}
+
+// block = 4 warps; warp w, lane l: link blockIdx.x * LPB + w * LPW + l / Nc, row l % Nc
+template <class R, int N>
+__device__ __forceinline__ void group_lane(int64_t first_link, int64_t Vh, int64_t& h, bool& active, int& r,
+                                           int& base, int& slot) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gi = lane / N;
+  r = lane - gi * N;
+  base = gi * N;
+  slot = warp * Group<R, N>::SLOTS + gi;
+  const int64_t link = first_link + int64_t(warp) * Group<R, N>::LPW + gi;
+  active = gi < Group<R, N>::LPW && link < Vh;
+  h = link < Vh ? link : Vh - 1;
+}
+
+template <class R, int N, int MODE>
+__global__ void __launch_bounds__(128) update_pass_group(const PassParams p) {
+  __shared__ Cpx<R> sm[Group<R, N>::WARPS * Group<R, N>::SLOTS][3][N][N];
+  int64_t h;
+  bool active;
+  int r, base, slot;
+  group_lane<R, N>(int64_t(blockIdx.x) * Group<R, N>::LPB, p.g.Vh, h, active, r, base, slot);
+  group_pass_body<R, N, MODE>(p, h, active, r, base, sm[slot]);
+}
+
 // FP64 passes of Nc >= 5 are built without the fused re-unitarization
 // (reunit_mode 1, 2): they would double the largest units' build time.
 template <class R, int N>
@@ -555,8 +882,9 @@ struct ReduceParams {
   double* partials;      // [gridDim.x * K]
   unsigned* counter;     // zero before the launch, zero after
   double* out;           // result slot base
-  const uint32_t* slot;  // optional: results go to out[(*slot % cap) * K + k]
+  const uint32_t* slot;  // optional: results go to out[((*slot % cap) * stride + offset) * K + k]
   int cap;
+  int stride, offset;    // row stride and column of a table of lattices (1, 0 for one lattice)
   double scale;
 };
 
@@ -595,7 +923,7 @@ __device__ __forceinline__ void reduce_finish(double (&v)[K], const ReduceParams
       for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
       if (lane == 0) {
         const int idx = rp.slot ? int(*rp.slot % uint32_t(rp.cap)) : 0;
-        rp.out[idx * K + k] = s * rp.scale;
+        rp.out[(int64_t(idx) * rp.stride + rp.offset) * K + k] = s * rp.scale;
       }
     }
     if (lane == 0) *rp.counter = 0u;
@@ -749,12 +1077,13 @@ __device__ __forceinline__ void batch_pass_body(const BatchParams& bp, int mu, i
     sp.reunit_rem = rrem;
   }
   __syncthreads();
+  const PassParams p = sp;  // a private copy: the body need not re-read shared memory
   const int64_t h = int64_t(blockIdx.x - first) * blockDim.x + threadIdx.x;
-  if (h >= sp.g.Vh) return;
+  if (h >= p.g.Vh) return;
   if constexpr (S == kQuat)
-    quat_pass_body<R, MODE, REUNIT>(sp, h);
+    quat_pass_body<R, MODE, REUNIT>(p, h);
   else
-    pass_body<R, N, S, MODE, (VAR & 2) != 0, REUNIT>(sp, h);
+    pass_body<R, N, S, MODE, (VAR & 2) != 0, REUNIT>(p, h);
 }
 
 template <class R, int N, int S, int MODE, int VAR, bool REUNIT>
@@ -768,6 +1097,37 @@ __global__ void __launch_bounds__(128, 6)
     update_pass_batch_occ(const BatchParams bp, int mu, int parity, uint32_t step_offset, uint32_t rmod,
                           uint32_t rrem) {
   batch_pass_body<R, N, S, MODE, VAR, REUNIT>(bp, mu, parity, step_offset, rmod, rrem);
+}
+
+template <class R, int N, int MODE>
+__global__ void __launch_bounds__(128)
+    update_pass_batch_group(const BatchParams bp, int mu, int parity, uint32_t step_offset) {
+  __shared__ PassParams sp;
+  __shared__ uint32_t first;
+  __shared__ Cpx<R> sm[Group<R, N>::WARPS * Group<R, N>::SLOTS][3][N][N];
+  if (threadIdx.x == 0) {
+    const int c = find_chain(bp.start, bp.n, blockIdx.x);
+    const ChainDesc& d = bp.chains[c];
+    first = bp.start[c];
+    sp.links = d.links;
+    sp.block_bytes = d.block_bytes;
+    sp.g = d.g;
+    sp.mu = mu;
+    sp.parity = parity;
+    sp.alpha_coef = d.alpha_coef;
+    sp.key = d.key;
+    sp.hb_step = d.hb_step;
+    sp.step_offset = step_offset;
+    sp.reunit_mod = 0u;
+    sp.reunit_rem = 0u;
+  }
+  __syncthreads();
+  const PassParams p = sp;  // a private copy: the body's __syncwarp()s would force re-reads of shared memory
+  int64_t h;
+  bool active;
+  int r, base, slot;
+  group_lane<R, N>(int64_t(blockIdx.x - first) * Group<R, N>::LPB, p.g.Vh, h, active, r, base, slot);
+  group_pass_body<R, N, MODE>(p, h, active, r, base, sm[slot]);
 }
 
 // stage the chain's observable parameters of this block in shared memory
@@ -987,6 +1347,16 @@ cudaError_t launch_pass(const Ctx& c, int mode, int mu, int parity, uint32_t ste
   const int bt = c.block_threads;
   const unsigned grid = unsigned((c.g.Vh + bt - 1) / bt);
   const bool ru = reunit_mod != 0u;
+  if constexpr (has_group<R, N>()) {
+    if (!ru && use_group<R, N>(c.variant)) {
+      const unsigned gg = unsigned((c.g.Vh + Group<R, N>::LPB - 1) / Group<R, N>::LPB);
+      if (mode == kHeatbathMode)
+        update_pass_group<R, N, kHeatbathMode><<<gg, 128, 0, c.stream>>>(p);
+      else
+        update_pass_group<R, N, kOverrelaxMode><<<gg, 128, 0, c.stream>>>(p);
+      return cudaGetLastError();
+    }
+  }
   if constexpr (!has_fused_reunit<R, N>()) {
     if (ru) return cudaErrorNotSupported;
     if (mode == kHeatbathMode)
@@ -1090,6 +1460,8 @@ cudaError_t launch_plaquette(const Ctx& c, double* out, const uint32_t* slot, in
   rp.out = out;
   rp.slot = slot;
   rp.cap = cap;
+  rp.stride = c.obs_stride;
+  rp.offset = c.obs_offset;
   rp.scale = 1.0 / (6.0 * double(c.g.V) * N);
   const int bt = 256;
   plaquette_kernel<R, N, S><<<reduce_grid(c, c.g.V, bt), bt, 0, c.stream>>>(make_obs_params(c), rp);
@@ -1104,6 +1476,8 @@ cudaError_t launch_polyakov(const Ctx& c, double* out, const uint32_t* slot, int
   rp.out = out;
   rp.slot = slot;
   rp.cap = cap;
+  rp.stride = c.obs_stride;
+  rp.offset = c.obs_offset;
   const int64_t nsp = int64_t(c.g.nx) * c.g.ny * c.g.nz;
   rp.scale = 1.0 / (double(N) * double(nsp));
   const int bt = 128;
@@ -1133,6 +1507,17 @@ cudaError_t launch_batch_pass(const BatchCtx& b, int mode, int mu, int parity, u
   if (b.n == 0) return cudaSuccess;
   const BatchParams bp{b.chains, b.pass_start, b.n};
   const bool ru = rmod != 0u;
+  if constexpr (has_group<R, N>()) {
+    if (!ru && use_group<R, N>(b.variant)) {
+      // the pass table of a group batch counts blocks of Group::LPB links
+      const BatchParams gp{b.chains, b.group_start, b.n};
+      if (mode == kHeatbathMode)
+        update_pass_batch_group<R, N, kHeatbathMode><<<b.group_blocks, 128, 0, b.stream>>>(gp, mu, parity, so);
+      else
+        update_pass_batch_group<R, N, kOverrelaxMode><<<b.group_blocks, 128, 0, b.stream>>>(gp, mu, parity, so);
+      return cudaGetLastError();
+    }
+  }
   const unsigned g1 = b.pass_blocks, bt = unsigned(b.pass_threads);
 #define SUN_LAUNCH_BATCH(K, V)                                                              \
   if (mode == kHeatbathMode) {                                                              \
@@ -1201,6 +1586,7 @@ const Ops* ops_instance() {
       int(sizeof(R)) * 8,
       Layout<R, N, S>::bytes,
       has_fused_reunit<R, N>() ? 1 : 0,
+      has_group<R, N>() && S == kFull ? Group<R, N>::LPB : 0,
       &launch_pass<R, N, S>,
       &launch_init<R, N, S>,
       &launch_reunit<R, N, S>,

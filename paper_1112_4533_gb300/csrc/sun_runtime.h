@@ -57,7 +57,8 @@ struct Ctx {
   cudaStream_t stream;
   int block_threads;
   int reduce_blocks;
-  int variant;  // update-pass kernel variant (bit 0: 6 blocks/SM register bound, bit 1: two-row staple)
+  int obs_stride, obs_offset;  // observable output: row stride and column (1, 0 for one lattice)
+  int variant;  // update-pass kernel variant (1: 6 blocks/SM bound, 2: two-row staple, 4: swap row-parallel / per-link kernel for Nc 4, 6)
 };
 
 // One chain (lattice) of a batch, as the batched kernels read it.
@@ -88,7 +89,8 @@ struct BatchCtx {
   const uint32_t* reunit_start;
   const uint32_t* plaq_start;
   const uint32_t* poly_start;
-  uint32_t pass_blocks, reunit_blocks, plaq_blocks, poly_blocks;
+  const uint32_t* group_start;  // pass table in blocks of group_links_per_block links (row-parallel kernel)
+  uint32_t pass_blocks, reunit_blocks, plaq_blocks, poly_blocks, group_blocks;
   int pass_threads;  // block size the pass table was built for
   int variant;
   double* partials;  // >= max(plaq_blocks, 2 * poly_blocks) doubles
@@ -99,6 +101,7 @@ struct BatchCtx {
 struct Ops {
   int nc, storage, precision, link_bytes;
   int fused_reunit;  // reunit_mode 1 and 2 built
+  int group_links_per_block;  // > 0: passes without re-unitarization use the row-parallel kernel
   cudaError_t (*pass)(const Ctx&, int mode, int mu, int parity, uint32_t step_offset, uint32_t reunit_mod,
                       uint32_t reunit_rem);
   cudaError_t (*init)(const Ctx&, int hot);

@@ -100,3 +100,25 @@ def test_batch_argument_errors(sunlib):
         sunlib.Batch([c])
     for L in (a, b, c):
         L.close()
+
+
+def test_large_chains_in_a_batch_run_as_alone(sunlib):
+    """Chains that fill the GPU on their own (here SU(3) 24^4 and SU(6) 16^4)
+    run the single-lattice kernels inside the batch; with small chains packed
+    beside them every chain still evolves exactly as alone."""
+    specs = [(3, (24, 24, 24, 24), 6.0, 31, 12, 32), (3, (4, 4, 4, 6), 5.8, 32, 12, 32),
+             (6, (16, 16, 16, 16), 25.0, 33, 72, 32), (6, (4, 4, 4, 4), 25.0, 34, 72, 32)]
+    alone = []
+    for spec in specs:
+        with make(sunlib, spec) as L:
+            plaq, poly = L.run(2, 1, 1)
+            alone.append((L.export_links(), plaq, poly))
+    lats = [make(sunlib, spec) for spec in specs]
+    with sunlib.Batch(lats) as B:
+        plaq, poly = B.run(2, 1, 1)
+    for i, L in enumerate(lats):
+        U, p1, l1 = alone[i]
+        assert np.array_equal(L.export_links(), U), i
+        assert np.abs(plaq[:, i] - p1).max() < 1e-12, i
+        assert np.abs(poly[:, i] - l1).max() < 1e-12, i
+        L.close()
