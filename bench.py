@@ -216,13 +216,21 @@ def barrier(world):
 
 
 def allreduce_max(x, world):
+    """Max of x over the ranks (the per-rank times of the timed region)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate_rate(units_per_rank, ms_local, world):
+    """Whole-job rate: the units all ranks processed over the slowest rank's time."""
+    ms = allreduce_max(ms_local, world)
+    return units_per_rank * world / (ms / 1e3), ms
 
 
 def time_kernel(L, reps):
@@ -275,8 +283,7 @@ def gpu_arm(args):
     torch.cuda.synchronize()
     clocks = sampler.stop()
     barrier(world)
-    ms_max = allreduce_max(ms, world)
-    value = updates_per_sweep() * K * world / (ms_max / 1e3)
+    value, ms_max = aggregate_rate(updates_per_sweep() * K, ms, world)
 
     # ---- dominant kernel, timed alone (events around each launch)
     k_ms = time_kernel(L, 32)
