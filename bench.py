@@ -271,8 +271,17 @@ def gpu_arm(args):
     V = volume(DIMS)
     hbm_peak, peak_kind = measured_peaks()
 
-    # ---- headline: FP32, two-row storage
-    kw = dict(precision=32, reunit_mode=args.reunit_mode, variant=args.variant)
+    # ---- headline: FP32; kernel shape, storage format and re-unitarization
+    # placement measured by the library's autotuner (outside the timed region)
+    tuned = None
+    if not args.no_tune:
+        t0 = time.perf_counter()
+        tuned = sun.autotune(NC, DIMS, BETA, N_HB, N_OR, precision=32, storage=args.storage,
+                             reunit_mode=args.reunit_mode, tune_storage=True, tune_reunit_mode=True)
+        tuned["tuning_s"] = time.perf_counter() - t0
+        args.storage, args.variant, args.reunit_mode = tuned["storage"], tuned["variant"], tuned["reunit_mode"]
+        args.block = tuned["block_threads"]
+    kw = dict(precision=32, reunit_mode=args.reunit_mode, variant=args.variant, block_threads=args.block)
     L = sun.Lattice(NC, DIMS, BETA, hot_start=False, seed=1 + rank, storage=args.storage, **kw)
     L.run(W, N_HB, N_OR)
     barrier(world)
@@ -300,8 +309,8 @@ def gpu_arm(args):
         del L
         torch.cuda.empty_cache()
         alt = 18 if args.storage == 12 else 12
-        for name, st, var in [(f"fp32_{alt}real", alt, args.variant),
-                              ("fp32_12real_two_row_staple", 12, args.variant | 2)]:
+        for name, st, var in [(f"fp32_{alt}real", alt, args.variant & ~2),
+                              ("fp32_12real_two_row_staple", 12, (args.variant | 2) & ~8)]:
             if st == args.storage and var == args.variant:
                 continue
             L2 = sun.Lattice(NC, DIMS, BETA, hot_start=False, seed=1 + rank, storage=st,
@@ -375,7 +384,8 @@ def gpu_arm(args):
         "data": "synthetic (cold start, Philox seed 1 + rank)",
         "config": {"workload": WORKLOAD_NAME, "nc": NC, "dims": list(DIMS), "beta": BETA,
                    "n_heatbath": N_HB, "n_overrelax": N_OR, "storage_reals": args.storage,
-                   "kernel_variant": args.variant,
+                   "kernel_variant": args.variant, "block_threads": args.block,
+                   "autotuned": tuned,
                    "reunitarize": ("FP64, every link once per sweep, " +
                                    {0: "own pass after the sweep", 1: "in the update kernels of the last step",
                                     2: "spread over the steps"}[args.reunit_mode]),
@@ -387,7 +397,8 @@ def gpu_arm(args):
         "polyakov_last": [float(poly[-1].real), float(poly[-1].imag)],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": traffic,
-                     "kernel": "update_pass_mat_occ<float,3,two-row,overrelax,variant 1>",
+                     "kernel": ("overrelaxation pass, SU(3) FP32 %d-real, kernel variant %d, one thread per link"
+                                % (args.storage, args.variant)),
                      "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": k_ms,
                      "peak_kind": peak_kind + " (hbm_gbs, copy kernel)"},
         "variants": variants,
@@ -414,7 +425,17 @@ def batched_arm(args):
     Ls = rng.choice([8, 12, 16, 24], size=n)
     betas = rng.uniform(5.6, 6.4, size=n)
     sweeps = 50
-    kw = dict(precision=32, storage=args.storage, reunit_mode=args.reunit_mode, variant=args.variant)
+    tuned = None
+    if not args.no_tune:
+        t0 = time.perf_counter()
+        tuned = sun.autotune_batch([(3, (int(L),) * 4, float(b)) for L, b in zip(Ls, betas)], 1, 4, precision=32,
+                                   storage=args.storage, reunit_mode=args.reunit_mode, tune_storage=True,
+                                   tune_reunit_mode=True)
+        tuned["tuning_s"] = time.perf_counter() - t0
+        args.storage, args.variant, args.reunit_mode = tuned["storage"], tuned["variant"], tuned["reunit_mode"]
+        args.block = tuned["block_threads"]
+    kw = dict(precision=32, storage=args.storage, reunit_mode=args.reunit_mode, variant=args.variant,
+              block_threads=args.block)
     lats = [sun.Lattice(3, (int(L),) * 4, float(b), hot_start=True, seed=100 + i, **kw)
             for i, (L, b) in enumerate(zip(Ls, betas))]
     updates = sum((1 + 4) * 4 * int(L) ** 4 for L in Ls) * sweeps
@@ -445,10 +466,10 @@ def batched_arm(args):
            "warmup": args.warmup, "ms_per_step": tb * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic (Haar starts, seeds 100..163)",
            "config": {"workload": "64 SU(3) chains, L in {8,12,16,24} (seeded draw), beta U[5.6,6.4], hot start, "
-                                  "50 sweeps of 1 heatbath + 4 overrelaxation each, FP32 two-row",
+                                  "50 sweeps of 1 heatbath + 4 overrelaxation each, FP32 links",
                       "L_counts": {str(v): int((Ls == v).sum()) for v in (8, 12, 16, 24)},
                       "link_updates_per_step": updates, "storage_reals": args.storage, "kernel_variant": args.variant,
-                      "reunit_mode": args.reunit_mode},
+                      "block_threads": args.block, "reunit_mode": args.reunit_mode, "autotuned": tuned},
            "link_updates_per_s": updates / tb,
            "plain": {"value": n / tpl, "unit": "chains/s", "ms_per_step": tpl * 1e3, "link_updates_per_s": updates / tpl,
                      "path": "each chain alone, sun_run of 50 sweeps (one captured sweep graph per chain)"},
@@ -521,7 +542,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--storage", type=int, default=12, choices=[12, 18])
-    ap.add_argument("--variant", type=int, default=1, choices=[0, 1, 2, 3],
+    ap.add_argument("--variant", type=int, default=1, choices=range(16),
                     help="update-kernel variant bits: 1 = 6 blocks/SM register bound, 2 = two-row staple")
     ap.add_argument("--reunit-mode", type=int, default=1, choices=[0, 1, 2])
     ap.add_argument("--e2e-steps", type=int, default=8)
@@ -529,6 +550,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="fixed configuration from the flags, no autotuning")
+    ap.add_argument("--block", type=int, default=0, help="threads per block of the update kernels (0 = 128)")
     ap.add_argument("--workload", choices=["single", "batched", "serving"], default="single")
     ap.add_argument("--requests", type=int, default=80)
     ap.add_argument("--budget-gb", type=float, default=64.0)

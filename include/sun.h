@@ -83,7 +83,15 @@ enum { SUN_HEATBATH = 0, SUN_OVERRELAX = 1 };
  *                links' unitarity drift, ~1e-6 between re-unitarizations);
  *                4 = (Nc = 4, 6) swap the pass kernel: by default Nc = 6 runs the
  *                row-parallel kernel (Nc threads per link) and Nc = 4 one thread
- *                per link.
+ *                per link;
+ *                8 = run the even and the odd pass of each direction as one
+ *                launch, a wavefront over t-slices: odd links of slice t are
+ *                updated once the even links of slices t-1, t, t+1 are done
+ *                (bitwise the same links as the two passes; the neighbour links
+ *                the two parities share are re-read from L2, not HBM).  Kernels
+ *                without this form (row-parallel, bit 2) run the two passes.
+ *                The device-side waits are bounded: one that gives up after
+ *                2 s makes sun_run / sun_synchronize return SUN_ERR_TIMEOUT.
  *  reunit_mode   where a sweep re-unitarizes (default 0); every link is
  *                re-unitarized once per re-unitarizing sweep in all three:
  *                0 = all links after the sweep's last step, as a pass of its own
@@ -93,6 +101,14 @@ enum { SUN_HEATBATH = 0, SUN_OVERRELAX = 1 };
  *                (lex >> 1), run r re-unitarized right after its update in step
  *                r mod (n_heatbath + n_overrelax), inside the update kernel.
  *                Modes 1 and 2 are not built for FP64 with Nc >= 5 (SUN_ERR_UNSUPPORTED).
+ *  wave_lag      with variant bit 8: t-slices the even units run ahead of the odd
+ *                ones (0 = default 3; clamped to [1, Nt-1]); results do not
+ *                depend on it.
+ *  wave_skip_units  fault injection for tests of the bounded waits, 0 in normal
+ *                use: every wavefront launch leaves out its first k units (even
+ *                links of slice 0 first), so the odd units that need them wait
+ *                until the 2 s limit and the lattice reports SUN_ERR_TIMEOUT;
+ *                the links it updates are then not valid.
  */
 typedef struct {
   int precision;
@@ -105,6 +121,8 @@ typedef struct {
   int use_graphs;
   int variant;
   int reunit_mode;
+  int wave_lag;
+  int wave_skip_units;
 } sun_options;
 
 int sun_abi_version(void);
@@ -216,6 +234,49 @@ sun_status sun_batch_create(sun_batch** out, sun_lattice* const* lattices, int n
 sun_status sun_batch_run(sun_batch* b, int n_sweeps, int n_heatbath, int n_overrelax, double* plaq,
                          double* poly);
 void sun_batch_destroy(sun_batch* b); /* syncs; the lattices are not touched */
+
+/* ---------------------------------------------------------------------------
+ * Autotuning.  The paper tunes its kernels by hand for its GPU (Sec. 3: threads
+ * per block, storage format, read path); here the configuration is measured on
+ * the GPU at hand.  Scratch lattices of the requested shape (hot start) are
+ * swept with each candidate configuration through sun_run / sun_batch_run and
+ * the fastest is kept.  The search goes one option at a time, each stage
+ * starting from the best of the previous one:
+ *   1. kernel shape: block_threads 64, 128, 256; variant bit 1 (SU(3) FP32);
+ *      per-link or row-parallel kernel (bit 4, Nc 4 and 6); with
+ *      SUN_TUNE_TWO_ROW also bit 2
+ *   2. with SUN_TUNE_STORAGE: storage (Nc = 2: 4 or 8 reals, Nc = 3: 12 or 18)
+ *   3. with SUN_TUNE_REUNIT_MODE: reunit_mode 0, 1, 2
+ *   4. variant bit 8 (wavefront launches), for kernels that have that form
+ * Bits 1, 4 and 8, block_threads and wave_lag leave the results bitwise
+ * unchanged; storage, reunit_mode and bit 2 change them at the level of FP32
+ * rounding (results stay within the FP32 tolerance of the FP64 oracle).
+ */
+enum {
+  SUN_TUNE_STORAGE = 1,
+  SUN_TUNE_REUNIT_MODE = 2,
+  SUN_TUNE_TWO_ROW = 4
+};
+
+/* Tune for one lattice of shape (nc, dims) at coupling beta swept with
+ * n_heatbath + n_overrelax steps per sweep.  *opt supplies precision,
+ * reunit_every, use_graphs, stream, wave_lag, and storage / reunit_mode where
+ * those are not tuned; on success the fastest configuration is written back
+ * into *opt (block_threads, variant, and the tuned fields) and, if
+ * ms_per_sweep is not NULL, its time per sweep.  device_buf must be NULL.
+ * Results are cached for the process by (device, shape, beta, steps, flags,
+ * fixed options): a repeated call returns at once.  Scratch lattices are
+ * created one at a time (sun_footprint_bytes each).  Syncs; takes about 30 ms
+ * of sweeps per candidate, 6 to 12 candidates. */
+sun_status sun_autotune(int nc, const int dims[4], double beta, int n_heatbath, int n_overrelax, int flags,
+                        sun_options* opt, double* ms_per_sweep);
+
+/* The same for a batch of n chains (nc[i], dims[4i .. 4i+3], beta[i]) swept
+ * together by sun_batch_run; every chain of the batch is to be created with the
+ * returned options.  The storage format is tuned only when all chains share Nc.
+ * The scratch lattices of all n chains exist at the same time. */
+sun_status sun_autotune_batch(int n, const int* nc, const int* dims, const double* beta, int n_heatbath,
+                              int n_overrelax, int flags, sun_options* opt, double* ms_per_sweep);
 
 /* Plaquette of link storage the caller already holds, with no allocation.
  * The paper has no counterpart: this entry point exists for callers that

@@ -47,6 +47,7 @@ sun_status fail(sun_status s, const char* fmt, ...) {
 
 constexpr size_t kAlign = 256;
 constexpr size_t kStagingCap = size_t(16) << 20;  // import/export chunk buffer
+constexpr int kDefaultWaveLag = 3;  // t-slices even units of a wavefront launch run ahead
 constexpr int kHistCap = 1024;                    // sweeps per observable-history chunk
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -78,7 +79,7 @@ sun_status check_dims(const int* dims) {
 }
 
 struct Plan {
-  size_t links_off, state_off, partials_off, results_off, hist_off, staging_off, total;
+  size_t links_off, state_off, wave_off, partials_off, results_off, hist_off, staging_off, total;
   size_t links_bytes, staging_bytes;
   int64_t staging_links;
 };
@@ -98,6 +99,8 @@ Plan make_plan(int nc, const int* dims, int link_bytes) {
   off = align_up(off + p.links_bytes, kAlign);
   p.state_off = off;
   off = align_up(off + sizeof(sun::DevState), kAlign);
+  p.wave_off = off;
+  off = align_up(off + (sun::kWaveSyncWords + size_t(dims[3])) * sizeof(uint32_t), kAlign);
   p.partials_off = off;
   off = align_up(off + 4 * sun::kMaxReduceBlocks * sizeof(double), kAlign);
   p.results_off = off;
@@ -175,6 +178,21 @@ sun_status check_launch(cudaError_t e, const char* what) {
   return SUN_OK;
 }
 
+// The eight passes of one step (mu = 0..3 x even, odd) on the lattice of c;
+// with variant bit 8 each direction's pair is one wavefront launch.
+sun_status enqueue_step(const sun::Ops* ops, const sun::Ctx& c, int mode, uint32_t step_offset, uint32_t mod,
+                        uint32_t rem) {
+  const char* what = mode == SUN_HEATBATH ? "heatbath pass" : "overrelaxation pass";
+  for (int mu = 0; mu < 4; ++mu) {
+    if ((c.variant & 8) && ops->pass_pair) {
+      SUN_TRY(check_launch(ops->pass_pair(c, mode, mu, step_offset, mod, rem), what));
+    } else {
+      for (int p = 0; p < 2; ++p) SUN_TRY(check_launch(ops->pass(c, mode, mu, p, step_offset, mod, rem), what));
+    }
+  }
+  return SUN_OK;
+}
+
 // Enqueue one sweep on stream s.  hist_mode: observables go to the history slot
 // held in device state, which is advanced at the end of the sweep.
 sun_status enqueue_sweep(sun_lattice* L, cudaStream_t s, int n_hb, int n_or, bool reunit, bool plaq,
@@ -192,10 +210,7 @@ sun_status enqueue_sweep(sun_lattice* L, cudaStream_t s, int n_hb, int n_or, boo
       mod = uint32_t(n_steps);
       rem = uint32_t(step);
     }
-    for (int mu = 0; mu < 4; ++mu)
-      for (int p = 0; p < 2; ++p)
-        SUN_TRY(check_launch(L->ops->pass(c, hb ? SUN_HEATBATH : SUN_OVERRELAX, mu, p, hb ? uint32_t(step) : 0u, mod, rem),
-                             hb ? "heatbath pass" : "overrelaxation pass"));
+    SUN_TRY(enqueue_step(L->ops, c, hb ? SUN_HEATBATH : SUN_OVERRELAX, hb ? uint32_t(step) : 0u, mod, rem));
   }
   if (reunit && !fused) SUN_TRY(check_launch(L->ops->reunit(c), "reunitarization"));
   const uint32_t* slot = hist_mode ? &L->ctx.state->slot : nullptr;
@@ -239,6 +254,19 @@ sun_status get_graph(sun_lattice* L, const GraphKey& key, cudaGraphExec_t* out) 
   return SUN_OK;
 }
 
+// Waits of wavefront launches that gave up (sync word 0, counted on the device):
+// report and clear them.  Call after the lattice's stream has synchronised.
+sun_status check_wave_timeouts(sun_lattice* L) {
+  if (!(L->ctx.variant & 8) || !L->ops->pass_pair) return SUN_OK;
+  uint32_t n = 0;
+  SUN_CUDA(cudaMemcpyAsync(&n, L->ctx.wave, sizeof(uint32_t), cudaMemcpyDeviceToHost, L->stream));
+  SUN_CUDA(cudaStreamSynchronize(L->stream));
+  if (n == 0) return SUN_OK;
+  SUN_CUDA(cudaMemsetAsync(L->ctx.wave, 0, sizeof(uint32_t), L->stream));
+  SUN_CUDA(cudaStreamSynchronize(L->stream));
+  return fail(SUN_ERR_TIMEOUT, "%u wavefront waits gave up after 2 s; the links updated since are not valid", n);
+}
+
 sun_status read_results(sun_lattice* L, int count) {
   SUN_CUDA(cudaMemcpyAsync(L->host_results, L->results, count * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
   SUN_CUDA(cudaStreamSynchronize(L->stream));
@@ -264,6 +292,8 @@ void sun_options_init(sun_options* opt) {
   opt->use_graphs = 1;
   opt->variant = 0;
   opt->reunit_mode = 0;
+  opt->wave_lag = 0;
+  opt->wave_skip_units = 0;
 }
 
 const char* sun_status_string(sun_status s) {
@@ -293,7 +323,10 @@ static sun_status resolve(int nc, const int* dims, const sun_options* opt_in, su
   if (opt->storage == 0) opt->storage = default_storage(nc);
   if (opt->reunit_every < 0) return fail(SUN_ERR_ARG, "reunit_every must be >= 0");
   if (opt->block_threads == 0) opt->block_threads = 128;
-  if (opt->variant < 0 || opt->variant > 7) return fail(SUN_ERR_ARG, "variant = %d must be in 0..7", opt->variant);
+  if (opt->variant < 0 || opt->variant > 15) return fail(SUN_ERR_ARG, "variant = %d must be in 0..15", opt->variant);
+  if (opt->wave_lag < 0) return fail(SUN_ERR_ARG, "wave_lag = %d must be >= 0", opt->wave_lag);
+  if (opt->wave_lag == 0) opt->wave_lag = kDefaultWaveLag;
+  if (opt->wave_skip_units < 0) return fail(SUN_ERR_ARG, "wave_skip_units must be >= 0");
   if (opt->reunit_mode < 0 || opt->reunit_mode > 2)
     return fail(SUN_ERR_ARG, "reunit_mode = %d must be 0, 1 or 2", opt->reunit_mode);
   if (opt->block_threads < 32 || opt->block_threads > 256 || (opt->block_threads & 31))
@@ -403,6 +436,9 @@ sun_status sun_lattice_create(sun_lattice** out, int nc, const int dims[4], doub
   c.stream = L->stream;
   c.block_threads = L->block_threads;
   c.variant = opt.variant;
+  c.wave = reinterpret_cast<uint32_t*>(L->base + L->plan.wave_off);
+  c.wave_lag = opt.wave_lag;
+  c.wave_skip = uint32_t(opt.wave_skip_units);
   c.obs_stride = 1;
   c.obs_offset = 0;
   int rb = 2 * (sms > 0 ? sms : 132);
@@ -411,7 +447,8 @@ sun_status sun_lattice_create(sun_lattice** out, int nc, const int dims[4], doub
   L->hist = reinterpret_cast<double*>(L->base + L->plan.hist_off);
   L->staging = reinterpret_cast<double*>(L->base + L->plan.staging_off);
 
-  if (cudaMemsetAsync(c.state, 0, sizeof(sun::DevState), L->stream) != cudaSuccess)
+  if (cudaMemsetAsync(c.state, 0, sizeof(sun::DevState), L->stream) != cudaSuccess ||
+      cudaMemsetAsync(c.wave, 0, (sun::kWaveSyncWords + size_t(dims[3])) * sizeof(uint32_t), L->stream) != cudaSuccess)
     return cleanup(fail(SUN_ERR_CUDA, "state reset failed"));
   sun_status st = check_launch(ops->init(ctx_on(L, L->stream), hot_start ? 1 : 0), "init");
   if (st != SUN_OK) return cleanup(st);
@@ -475,7 +512,7 @@ sun_status sun_run(sun_lattice* L, int n_sweeps, int n_hb, int n_or, double* pla
     done += chunk;
   }
   SUN_CUDA(cudaStreamSynchronize(L->stream));
-  return SUN_OK;
+  return check_wave_timeouts(L);
 }
 
 sun_status sun_reunitarize(sun_lattice* L) {
@@ -599,7 +636,7 @@ sun_status sun_synchronize(sun_lattice* L) {
   if (!L) return fail(SUN_ERR_ARG, "lattice is NULL");
   SUN_TRY(set_device(L));
   SUN_CUDA(cudaStreamSynchronize(L->stream));
-  return SUN_OK;
+  return check_wave_timeouts(L);
 }
 
 sun_status sun_get_info(const sun_lattice* L, sun_lattice_info* info) {
@@ -701,14 +738,14 @@ sun_status enqueue_batch_sweep(sun_batch* B, cudaStream_t s, int n_hb, int n_or,
         mod = uint32_t(n_steps);
         rem = uint32_t(step);
       }
-      for (int mu = 0; mu < 4; ++mu)
-        for (int p = 0; p < 2; ++p) {
-          const int mode = hb ? SUN_HEATBATH : SUN_OVERRELAX;
-          const uint32_t so = hb ? uint32_t(step) : 0u;
-          if (g.n_small > 0) SUN_TRY(check_launch(g.ops->batch_pass(c, mode, mu, p, so, mod, rem), "batched pass"));
-          for (size_t k = size_t(g.n_small); k < g.members.size(); ++k)
-            SUN_TRY(check_launch(g.ops->pass(ctx_on(g.members[k], g.stream), mode, mu, p, so, mod, rem), "pass"));
-        }
+      const int mode = hb ? SUN_HEATBATH : SUN_OVERRELAX;
+      const uint32_t so = hb ? uint32_t(step) : 0u;
+      if (g.n_small > 0)
+        for (int mu = 0; mu < 4; ++mu)
+          for (int p = 0; p < 2; ++p)
+            SUN_TRY(check_launch(g.ops->batch_pass(c, mode, mu, p, so, mod, rem), "batched pass"));
+      for (size_t k = size_t(g.n_small); k < g.members.size(); ++k)
+        SUN_TRY(enqueue_step(g.ops, ctx_on(g.members[k], g.stream), mode, so, mod, rem));
     }
     const uint32_t* slot = hist_mode ? B->d_slot : nullptr;
     double* hist_p = B->d_hist;
@@ -996,6 +1033,8 @@ sun_status sun_batch_run(sun_batch* B, int n_sweeps, int n_hb, int n_or, double*
   SUN_CUDA(cudaStreamSynchronize(B->stream));
   B->sweeps_done += uint64_t(n_sweeps);
   for (sun_lattice* L : B->lattices) L->sweeps_done += uint64_t(n_sweeps);
+  for (const auto& g : B->groups)
+    for (size_t k = size_t(g.n_small); k < g.members.size(); ++k) SUN_TRY(check_wave_timeouts(g.members[k]));
   return SUN_OK;
 }
 

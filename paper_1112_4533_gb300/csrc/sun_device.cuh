@@ -336,8 +336,19 @@ __device__ __forceinline__ void unpack(double2 v, double* r) { r[0] = v.x; r[1] 
 __device__ __forceinline__ float4 pack4(const float* r) { return make_float4(r[0], r[1], r[2], r[3]); }
 __device__ __forceinline__ double2 pack4(const double* r) { return make_double2(r[0], r[1]); }
 
-// read the stored reals of half-site h of a block (read-only path)
-template <class R, int NR, bool kNc>
+// How a link is loaded: kLoadPlain (ld.global), kLoadNc (read-only data path,
+// only for links no thread writes while the kernel runs), kLoadCg (cached in L2
+// only: links another block of the same kernel may have written before a
+// synchronisation)
+enum LoadKind { kLoadPlain = 0, kLoadNc = 1, kLoadCg = 2 };
+
+template <class V>
+__device__ __forceinline__ V load_as(const V* p, int kind) {
+  return kind == kLoadNc ? __ldg(p) : (kind == kLoadCg ? __ldcg(p) : *p);
+}
+
+// read the stored reals of half-site h of a block
+template <class R, int NR, int kLoad>
 __device__ __forceinline__ void load_reals(const char* __restrict__ blk, int64_t Vh, int64_t h, R (&r)[NR]) {
   constexpr int per16 = 16 / int(sizeof(R));
   constexpr int n16 = NR / per16;
@@ -345,12 +356,12 @@ __device__ __forceinline__ void load_reals(const char* __restrict__ blk, int64_t
 #pragma unroll
   for (int c = 0; c < n16; ++c) {
     const V* p = reinterpret_cast<const V*>(blk + (int64_t(c) * Vh + h) * 16);
-    V v = kNc ? __ldg(p) : *p;
+    V v = load_as(p, kLoad);
     unpack(v, &r[c * per16]);
   }
   if constexpr (NR % per16 != 0) {
     const float2* p = reinterpret_cast<const float2*>(blk + int64_t(n16) * Vh * 16 + h * 8);
-    float2 v = kNc ? __ldg(p) : *p;
+    float2 v = load_as(p, kLoad);
     r[NR - 2] = v.x;
     r[NR - 1] = v.y;
   }
@@ -414,10 +425,10 @@ __device__ __forceinline__ void mat_to_reals(const Mat<R, N>& m, R (&r)[Layout<R
   }
 }
 
-template <class R, int N, int S, bool kNc = true>
+template <class R, int N, int S, int kLoad = kLoadNc>
 __device__ __forceinline__ Mat<R, N> load_mat(const char* blk, int64_t Vh, int64_t h) {
   R r[Layout<R, N, S>::nreals];
-  load_reals<R, Layout<R, N, S>::nreals, kNc>(blk, Vh, h, r);
+  load_reals<R, Layout<R, N, S>::nreals, kLoad>(blk, Vh, h, r);
   Mat<R, N> m;
   reals_to_mat<R, N, S>(r, m);
   return m;
@@ -430,10 +441,10 @@ __device__ __forceinline__ void store_mat(char* blk, int64_t Vh, int64_t h, cons
   store_reals<R, Layout<R, N, S>::nreals>(blk, Vh, h, r);
 }
 
-template <class R, bool kNc = true>
+template <class R, int kLoad = kLoadNc>
 __device__ __forceinline__ Quat<R> load_quat(const char* blk, int64_t Vh, int64_t h) {
   R r[4];
-  load_reals<R, 4, kNc>(blk, Vh, h, r);
+  load_reals<R, 4, kLoad>(blk, Vh, h, r);
   return {r[0], r[1], r[2], r[3]};
 }
 

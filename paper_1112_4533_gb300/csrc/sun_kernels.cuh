@@ -192,7 +192,7 @@ struct Rows2 {
 template <class R>
 __device__ __forceinline__ Rows2<R> load_rows2(const char* blk, int64_t Vh, int64_t h) {
   R r[12];
-  load_reals<R, 12, true>(blk, Vh, h, r);
+  load_reals<R, 12, kLoadNc>(blk, Vh, h, r);
   Rows2<R> m;
 #pragma unroll
   for (int i = 0; i < 2; ++i)
@@ -201,13 +201,13 @@ __device__ __forceinline__ Rows2<R> load_rows2(const char* blk, int64_t Vh, int6
   return m;
 }
 
-// U_nu(x) U_mu(x+nu) U_nu(x+mu)^+ added to st
-template <class R, int N, int S, bool ROWS2>
+// U_nu(x) U_mu(x+nu) U_nu(x+mu)^+ added to st; BL: how U_mu is loaded
+template <class R, int N, int S, bool ROWS2, int BL>
 __device__ __forceinline__ void staple_forward(Mat<R, N>& st, const char* pa, int64_t ha, const char* pb, int64_t hb,
                                                const char* pc, int64_t hc, int64_t Vh) {
   if constexpr (S == kTwoRow && ROWS2) {
     const Rows2<R> a = load_rows2<R>(pa, Vh, ha);
-    const Mat<R, 3> b = load_mat<R, 3, S>(pb, Vh, hb);
+    const Mat<R, 3> b = load_mat<R, 3, S, BL>(pb, Vh, hb);
     Cpx<R> ab[2][3];
 #pragma unroll
     for (int i = 0; i < 2; ++i)
@@ -239,15 +239,15 @@ __device__ __forceinline__ void staple_forward(Mat<R, N>& st, const char* pa, in
       }
   } else {
     const Mat<R, N> a = load_mat<R, N, S>(pa, Vh, ha);
-    const Mat<R, N> b = load_mat<R, N, S>(pb, Vh, hb);
+    const Mat<R, N> b = load_mat<R, N, S, BL>(pb, Vh, hb);
     const Mat<R, N> t = mul_nn(a, b);
     const Mat<R, N> c = load_mat<R, N, S>(pc, Vh, hc);
     acc_nd(st, t, c);
   }
 }
 
-// U_nu(x-nu)^+ U_mu(x-nu) U_nu(x-nu+mu) added to st
-template <class R, int N, int S, bool ROWS2>
+// U_nu(x-nu)^+ U_mu(x-nu) U_nu(x-nu+mu) added to st; BL: how U_mu is loaded
+template <class R, int N, int S, bool ROWS2, int BL>
 __device__ __forceinline__ void staple_backward(Mat<R, N>& st, const char* pa, int64_t ha, const char* pb, int64_t hb,
                                                 const char* pc, int64_t hc, int64_t Vh) {
   if constexpr (S == kTwoRow && ROWS2) {
@@ -260,7 +260,7 @@ __device__ __forceinline__ void staple_backward(Mat<R, N>& st, const char* pa, i
       const Cpx<R> u = cmul(a.e[0][2], a.e[1][0]), v = cmul(a.e[0][0], a.e[1][2]);
       a21 = {u.re - v.re, -(u.im - v.im)};
     }
-    const Mat<R, 3> b = load_mat<R, 3, S>(pb, Vh, hb);
+    const Mat<R, 3> b = load_mat<R, 3, S, BL>(pb, Vh, hb);
     // rows 0,1 of a^+ b: (a^+ b)_ik = sum_m conj(a_mi) b_mk
     Cpx<R> d[2][3];
 #pragma unroll
@@ -295,7 +295,7 @@ __device__ __forceinline__ void staple_backward(Mat<R, N>& st, const char* pa, i
       }
   } else {
     const Mat<R, N> a = load_mat<R, N, S>(pa, Vh, ha);
-    const Mat<R, N> b = load_mat<R, N, S>(pb, Vh, hb);
+    const Mat<R, N> b = load_mat<R, N, S, BL>(pb, Vh, hb);
     const Mat<R, N> t = mul_dn(a, b);
     const Mat<R, N> c = load_mat<R, N, S>(pc, Vh, hc);
     acc_nn(st, t, c);
@@ -308,16 +308,19 @@ __device__ __forceinline__ void staple_backward(Mat<R, N>& st, const char* pa, i
 // (Eq. 15), heatbath (Eqs. 12-14) or overrelaxation (Eq. 17) -> store.
 // One thread per link of the pass.
 // ---------------------------------------------------------------------------
-template <class R, int N, int S, int MODE, bool ROWS2, bool REUNIT>
-__device__ __forceinline__ void pass_body(const PassParams& p, int64_t h) {
+// COH: the links of direction mu on the other parity may have been written by
+// another block of the same launch (wavefront launches): they are read through L2.
+template <class R, int N, int S, int MODE, bool ROWS2, bool REUNIT, bool COH = false>
+__device__ __forceinline__ void pass_body(const PassParams& p, int par, int64_t h) {
   const Geom& g = p.g;
-  const int mu = p.mu, par = p.parity, opp = par ^ 1;
+  const int mu = p.mu, opp = par ^ 1;
   const Site s = decode_half(g, h, par);
   const uint32_t lex = uint32_t(s.lex);
   const int cmu = coord_of(s, mu);
   const uint32_t lex_pmu = fwd(g, lex, cmu, mu);
 
 
+  constexpr int BL = COH ? kLoadCg : kLoadNc;  // U_mu of the other parity
   Mat<R, N> st;
   mat_zero(st);
 #pragma unroll
@@ -327,14 +330,14 @@ __device__ __forceinline__ void pass_body(const PassParams& p, int64_t h) {
     const uint32_t lex_pnu = fwd(g, lex, cnu, nu);
     const uint32_t lex_mnu = bwd(g, lex, cnu, nu);
     const uint32_t lex_mnu_pmu = fwd(g, lex_mnu, cmu, mu);
-    staple_forward<R, N, S, ROWS2>(st, block_ptr(p, nu, par), h, block_ptr(p, mu, opp), lex_pnu >> 1,
-                                   block_ptr(p, nu, opp), lex_pmu >> 1, g.Vh);
-    staple_backward<R, N, S, ROWS2>(st, block_ptr(p, nu, opp), lex_mnu >> 1, block_ptr(p, mu, opp), lex_mnu >> 1,
-                                    block_ptr(p, nu, par), lex_mnu_pmu >> 1, g.Vh);
+    staple_forward<R, N, S, ROWS2, BL>(st, block_ptr(p, nu, par), h, block_ptr(p, mu, opp), lex_pnu >> 1,
+                                       block_ptr(p, nu, opp), lex_pmu >> 1, g.Vh);
+    staple_backward<R, N, S, ROWS2, BL>(st, block_ptr(p, nu, opp), lex_mnu >> 1, block_ptr(p, mu, opp),
+                                        lex_mnu >> 1, block_ptr(p, nu, par), lex_mnu_pmu >> 1, g.Vh);
   }
 
   char* ublk = p.links + (2 * mu + par) * p.block_bytes;
-  Mat<R, N> u = load_mat<R, N, S, false>(ublk, g.Vh, h);
+  Mat<R, N> u = load_mat<R, N, S, kLoadPlain>(ublk, g.Vh, h);
   Mat<R, N> w = mul_nd(u, st);
 
   uint32_t step = 0;
@@ -388,14 +391,14 @@ template <class R, int N, int S, int MODE, int VAR, bool REUNIT>
 __global__ void __launch_bounds__(kMaxBlockThreads) update_pass_mat(const PassParams p) {
   const int64_t h = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (h >= p.g.Vh) return;
-  pass_body<R, N, S, MODE, (VAR & 2) != 0, REUNIT>(p, h);
+  pass_body<R, N, S, MODE, (VAR & 2) != 0, REUNIT>(p, p.parity, h);
 }
 
 template <class R, int N, int S, int MODE, int VAR, bool REUNIT>
 __global__ void __launch_bounds__(128, 6) update_pass_mat_occ(const PassParams p) {
   const int64_t h = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (h >= p.g.Vh) return;
-  pass_body<R, N, S, MODE, (VAR & 2) != 0, REUNIT>(p, h);
+  pass_body<R, N, S, MODE, (VAR & 2) != 0, REUNIT>(p, p.parity, h);
 }
 
 // ---------------------------------------------------------------------------
@@ -742,10 +745,11 @@ constexpr bool has_variants() {
 // One chessboard pass for SU(2) stored as quaternions (Eq. 6): the same steps
 // with the staple kept in the real span of SU(2).
 // ---------------------------------------------------------------------------
-template <class R, int MODE, bool REUNIT>
-__device__ __forceinline__ void quat_pass_body(const PassParams& p, int64_t h) {
+template <class R, int MODE, bool REUNIT, bool COH = false>
+__device__ __forceinline__ void quat_pass_body(const PassParams& p, int par, int64_t h) {
+  constexpr int BL = COH ? kLoadCg : kLoadNc;  // U_mu of the other parity
   const Geom& g = p.g;
-  const int mu = p.mu, par = p.parity, opp = par ^ 1;
+  const int mu = p.mu, opp = par ^ 1;
   const Site s = decode_half(g, h, par);
   const uint32_t lex = uint32_t(s.lex);
   const int cmu = coord_of(s, mu);
@@ -761,19 +765,19 @@ __device__ __forceinline__ void quat_pass_body(const PassParams& p, int64_t h) {
     const uint32_t lex_mnu_pmu = fwd(g, lex_mnu, cmu, mu);
     {
       const Quat<R> a = load_quat<R>(block_ptr(p, nu, par), g.Vh, h);
-      const Quat<R> b = load_quat<R>(block_ptr(p, mu, opp), g.Vh, lex_pnu >> 1);
+      const Quat<R> b = load_quat<R, BL>(block_ptr(p, mu, opp), g.Vh, lex_pnu >> 1);
       const Quat<R> c = load_quat<R>(block_ptr(p, nu, opp), g.Vh, lex_pmu >> 1);
       st = qadd(st, qmul(qmul(a, b), qdag(c)));
     }
     {
       const Quat<R> a = load_quat<R>(block_ptr(p, nu, opp), g.Vh, lex_mnu >> 1);
-      const Quat<R> b = load_quat<R>(block_ptr(p, mu, opp), g.Vh, lex_mnu >> 1);
+      const Quat<R> b = load_quat<R, BL>(block_ptr(p, mu, opp), g.Vh, lex_mnu >> 1);
       const Quat<R> c = load_quat<R>(block_ptr(p, nu, par), g.Vh, lex_mnu_pmu >> 1);
       st = qadd(st, qmul(qmul(qdag(a), b), c));
     }
   }
   char* ublk = p.links + (2 * mu + par) * p.block_bytes;
-  Quat<R> u = load_quat<R, false>(ublk, g.Vh, h);
+  Quat<R> u = load_quat<R, kLoadPlain>(ublk, g.Vh, h);
   const Quat<R> w = qmul(u, qdag(st));
   const R k = d_sqrt(fma(w.a0, w.a0, fma(w.a1, w.a1, fma(w.a2, w.a2, w.a3 * w.a3))));
   if (k > R(1e-15) && d_isfinite(k)) {
@@ -802,7 +806,135 @@ template <class R, int MODE, bool REUNIT>
 __global__ void __launch_bounds__(kMaxBlockThreads) update_pass_quat(const PassParams p) {
   const int64_t h = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (h >= p.g.Vh) return;
-  quat_pass_body<R, MODE, REUNIT>(p, h);
+  quat_pass_body<R, MODE, REUNIT>(p, p.parity, h);
+}
+
+// ---------------------------------------------------------------------------
+// Both parities of one direction in one launch (the even and odd pass of a
+// step, Sec. 3), as a wavefront over t-slices.
+//
+// One block per unit of (parity, t-slice, chunk of blockDim.x links); a block
+// takes its unit from a ticket counter when it starts.  The staple (Eq. 9) of an
+// odd link on slice t reads the even links of the same direction on slices t-1,
+// t, t+1, so an odd unit first waits until those three even slices are
+// finished; even units wait for nothing.  Even slices run `lag` slices ahead of
+// the odd ones, and odd slice 0, which needs the last even slice, comes last.
+// Every wait is on units with smaller tickets, all held by blocks that have
+// started, so the launch progresses however many blocks are resident.  Each
+// link sees the same neighbour values as in two separate passes (all even
+// links, then all odd links), so the results are bitwise those of the
+// two-launch schedule; the links a slice's even and odd
+// units share are still in L2 when the odd unit reads them.
+// ---------------------------------------------------------------------------
+struct WaveParams {
+  uint32_t* sync;       // [0] wait timeouts, [1] ticket, [2 + t] finished even units of slice t
+  uint32_t chunks;      // chunks per (parity, slice) = ceil(half_slice / blockDim.x)
+  uint32_t half_slice;  // sites of one parity on one t-slice, Nx Ny Nz / 2
+  uint32_t nt;
+  uint32_t lag;   // 1 <= lag <= nt - 1
+  uint32_t skip;  // units left out at the start (fault injection for tests; 0 otherwise)
+};
+
+constexpr uint64_t kWaveWaitNs = 2000000000ull;  // give up a wait after 2 s
+constexpr uint32_t kWaveWaitPolls = 1u << 24;   // or after this many polls
+
+// Unit j (0 <= j < 2 nt) of the issue order: E0 .. E(lag), then E(k), O(k - lag)
+// for k = lag+1 .. nt-1, then O(nt - lag) .. O(nt - 1), then O(0).
+__host__ __device__ __forceinline__ void wave_unit(uint32_t j, uint32_t nt, uint32_t lag, int& par, uint32_t& t) {
+  if (j <= lag) {
+    par = 0;
+    t = j;
+  } else if (j + lag + 2 <= 2 * nt) {
+    const bool even = ((j - lag - 1) & 1u) == 0u;
+    par = even ? 0 : 1;
+    t = even ? (j + lag + 1) / 2 : (j - lag) / 2;
+  } else {
+    par = 1;
+    t = j == 2 * nt - 1 ? 0u : j + 1 - nt;
+  }
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* a) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Thread 0: wait until the even slices t-1, t, t+1 are finished.  The wait is
+// bounded; one that gives up is counted in sync[2] and the unit goes ahead.
+__device__ __forceinline__ void wave_wait_even(const WaveParams& w, uint32_t t) {
+  const uint32_t ts[3] = {t == 0 ? w.nt - 1 : t - 1, t, t + 1 == w.nt ? 0u : t + 1};
+  uint64_t t0 = 0;
+  uint32_t polls = 0;
+  for (int q = 0; q < 3; ++q) {
+    const uint32_t* cnt = w.sync + kWaveSyncWords + ts[q];
+    while (ld_acquire_gpu(cnt) < w.chunks) {
+      const uint64_t now = global_timer_ns();
+      if (polls == 0) t0 = now;
+      if (++polls > kWaveWaitPolls || now - t0 > kWaveWaitNs) {
+        atomicAdd(w.sync, 1u);
+        return;
+      }
+      __nanosleep(256);
+    }
+  }
+  __threadfence();
+}
+
+// QUAT: the body is the quaternion SU(2) pass, else the matrix pass.  (The body is
+// called directly, not through a lambda: a lambda holding a reference to the
+// kernel parameters would copy them to local memory.)
+template <class R, int N, int S, int MODE, bool ROWS2, bool REUNIT, bool QUAT>
+__device__ __forceinline__ void wavefront(const PassParams& p, const WaveParams& w) {
+  __shared__ uint32_t s_ticket;
+  if (threadIdx.x == 0) s_ticket = atomicAdd(w.sync + 1, 1u);
+  __syncthreads();
+  const uint32_t ticket = s_ticket + w.skip;
+  const bool valid = ticket < 2u * w.nt * w.chunks;  // false only if the counter was disturbed
+  const uint32_t j = ticket / w.chunks, c = ticket - j * w.chunks;
+  int par = 0;
+  uint32_t t = 0;
+  if (valid) wave_unit(j, w.nt, w.lag, par, t);
+  if (par == 1) {
+    if (threadIdx.x == 0) wave_wait_even(w, t);
+    __syncthreads();
+  }
+  const uint32_t i = c * blockDim.x + threadIdx.x;
+  if (valid && i < w.half_slice) {
+    const int64_t h = int64_t(t) * w.half_slice + i;
+    if constexpr (QUAT)
+      quat_pass_body<R, MODE, REUNIT, true>(p, par, h);
+    else
+      pass_body<R, N, S, MODE, ROWS2, REUNIT, true>(p, par, h);
+  }
+  if (valid && par == 0) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();  // the block's link stores before the count that publishes them
+      atomicAdd(w.sync + kWaveSyncWords + t, 1u);
+    }
+  }
+}
+
+template <class R, int N, int S, int MODE, int VAR, bool REUNIT>
+__global__ void __launch_bounds__(kMaxBlockThreads) update_pair_mat(const PassParams p, const WaveParams w) {
+  wavefront<R, N, S, MODE, (VAR & 2) != 0, REUNIT, false>(p, w);
+}
+
+template <class R, int N, int S, int MODE, int VAR, bool REUNIT>
+__global__ void __launch_bounds__(128, 6) update_pair_mat_occ(const PassParams p, const WaveParams w) {
+  wavefront<R, N, S, MODE, (VAR & 2) != 0, REUNIT, false>(p, w);
+}
+
+template <class R, int MODE, bool REUNIT>
+__global__ void __launch_bounds__(kMaxBlockThreads) update_pair_quat(const PassParams p, const WaveParams w) {
+  wavefront<R, 2, kQuat, MODE, false, REUNIT, true>(p, w);
 }
 
 struct LinkParams {
@@ -821,12 +953,12 @@ __global__ void __launch_bounds__(256) reunit_kernel(const LinkParams p) {
   const int64_t h = idx - int64_t(b) * p.g.Vh;
   char* blk = p.links + b * p.block_bytes;
   if constexpr (S == kQuat) {
-    const Quat<R> q = load_quat<R, false>(blk, p.g.Vh, h);
+    const Quat<R> q = load_quat<R, kLoadPlain>(blk, p.g.Vh, h);
     const double a0 = q.a0, a1 = q.a1, a2 = q.a2, a3 = q.a3;
     const double inv = rsqrt(a0 * a0 + a3 * a3 + a2 * a2 + a1 * a1);
     store_quat<R>(blk, p.g.Vh, h, Quat<R>{R(a0 * inv), R(a1 * inv), R(a2 * inv), R(a3 * inv)});
   } else {
-    Mat<double, N> m = mat_cast<R, double, N>(load_mat<R, N, S, false>(blk, p.g.Vh, h));
+    Mat<double, N> m = mat_cast<R, double, N>(load_mat<R, N, S, kLoadPlain>(blk, p.g.Vh, h));
     reunit_d<N>(m);
     store_mat<R, N, S>(blk, p.g.Vh, h, mat_cast<double, R, N>(m));
   }
@@ -1081,9 +1213,9 @@ __device__ __forceinline__ void batch_pass_body(const BatchParams& bp, int mu, i
   const int64_t h = int64_t(blockIdx.x - first) * blockDim.x + threadIdx.x;
   if (h >= p.g.Vh) return;
   if constexpr (S == kQuat)
-    quat_pass_body<R, MODE, REUNIT>(p, h);
+    quat_pass_body<R, MODE, REUNIT>(p, p.parity, h);
   else
-    pass_body<R, N, S, MODE, (VAR & 2) != 0, REUNIT>(p, h);
+    pass_body<R, N, S, MODE, (VAR & 2) != 0, REUNIT>(p, p.parity, h);
 }
 
 template <class R, int N, int S, int MODE, int VAR, bool REUNIT>
@@ -1154,12 +1286,12 @@ __global__ void __launch_bounds__(128) reunit_batch(const BatchParams bp) {
   const int64_t h = idx - int64_t(b) * sp.g.Vh;
   char* blk = const_cast<char*>(sp.links) + b * sp.block_bytes;
   if constexpr (S == kQuat) {
-    const Quat<R> q = load_quat<R, false>(blk, sp.g.Vh, h);
+    const Quat<R> q = load_quat<R, kLoadPlain>(blk, sp.g.Vh, h);
     const double a0 = q.a0, a1 = q.a1, a2 = q.a2, a3 = q.a3;
     const double inv = rsqrt(a0 * a0 + a3 * a3 + a2 * a2 + a1 * a1);
     store_quat<R>(blk, sp.g.Vh, h, Quat<R>{R(a0 * inv), R(a1 * inv), R(a2 * inv), R(a3 * inv)});
   } else {
-    Mat<double, N> m = mat_cast<R, double, N>(load_mat<R, N, S, false>(blk, sp.g.Vh, h));
+    Mat<double, N> m = mat_cast<R, double, N>(load_mat<R, N, S, kLoadPlain>(blk, sp.g.Vh, h));
     reunit_d<N>(m);
     store_mat<R, N, S>(blk, sp.g.Vh, h, mat_cast<double, R, N>(m));
   }
@@ -1414,6 +1546,79 @@ cudaError_t launch_pass(const Ctx& c, int mode, int mu, int parity, uint32_t ste
   return cudaGetLastError();
 }
 
+// A wavefront launch: the ticket and the slice counters are cleared first, then
+// one block per unit; blocks take their unit from the ticket counter in the
+// order they start.
+template <class K>
+cudaError_t launch_wave(K kernel, int bt, const Ctx& c, const PassParams& p, const WaveParams& w) {
+  const cudaError_t e = cudaMemsetAsync(w.sync + 1, 0, (kWaveSyncWords - 1 + size_t(w.nt)) * sizeof(uint32_t), c.stream);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = 2u * w.nt * w.chunks - w.skip;
+  kernel<<<grid, bt, 0, c.stream>>>(p, w);
+  return cudaGetLastError();
+}
+
+template <class R, int N, int S, int VAR>
+cudaError_t launch_pair_mat(const Ctx& c, int mode, bool ru, int bt, const PassParams& p, const WaveParams& w) {
+  const bool hb = mode == kHeatbathMode;
+  if constexpr (!has_fused_reunit<R, N>()) {
+    if (ru) return cudaErrorNotSupported;
+    return hb ? launch_wave(update_pair_mat<R, N, S, kHeatbathMode, VAR, false>, bt, c, p, w)
+              : launch_wave(update_pair_mat<R, N, S, kOverrelaxMode, VAR, false>, bt, c, p, w);
+  } else if constexpr ((VAR & 1) != 0) {
+    if (hb)
+      return ru ? launch_wave(update_pair_mat_occ<R, N, S, kHeatbathMode, VAR, true>, bt, c, p, w)
+                : launch_wave(update_pair_mat_occ<R, N, S, kHeatbathMode, VAR, false>, bt, c, p, w);
+    return ru ? launch_wave(update_pair_mat_occ<R, N, S, kOverrelaxMode, VAR, true>, bt, c, p, w)
+              : launch_wave(update_pair_mat_occ<R, N, S, kOverrelaxMode, VAR, false>, bt, c, p, w);
+  } else {
+    if (hb)
+      return ru ? launch_wave(update_pair_mat<R, N, S, kHeatbathMode, VAR, true>, bt, c, p, w)
+                : launch_wave(update_pair_mat<R, N, S, kHeatbathMode, VAR, false>, bt, c, p, w);
+    return ru ? launch_wave(update_pair_mat<R, N, S, kOverrelaxMode, VAR, true>, bt, c, p, w)
+              : launch_wave(update_pair_mat<R, N, S, kOverrelaxMode, VAR, false>, bt, c, p, w);
+  }
+}
+
+// The even and the odd pass of direction mu.  Kernels without a wavefront form
+// (the row-parallel kernel, the two-row staple variant) run as the two passes.
+template <class R, int N, int S>
+cudaError_t launch_pair(const Ctx& c, int mode, int mu, uint32_t step_offset, uint32_t reunit_mod,
+                        uint32_t reunit_rem) {
+  const bool ru = reunit_mod != 0u;
+  bool two = !c.wave;
+  if constexpr (has_group<R, N>()) two = two || (!ru && use_group<R, N>(c.variant));
+  if constexpr (has_variants<R, N, S>()) two = two || (c.variant & 2) != 0;
+  if (two) {
+    const cudaError_t e = launch_pass<R, N, S>(c, mode, mu, 0, step_offset, reunit_mod, reunit_rem);
+    if (e != cudaSuccess) return e;
+    return launch_pass<R, N, S>(c, mode, mu, 1, step_offset, reunit_mod, reunit_rem);
+  }
+  const PassParams p = make_pass_params(c, mu, 0, step_offset, reunit_mod, reunit_rem);
+  bool occ = false;
+  if constexpr (has_variants<R, N, S>()) occ = (c.variant & 1) != 0;
+  const int bt = occ ? 128 : c.block_threads;
+  WaveParams w;
+  w.sync = c.wave;
+  w.half_slice = uint32_t(int64_t(c.g.nx) * c.g.ny * c.g.nz / 2);
+  w.nt = uint32_t(c.g.nt);
+  w.chunks = (w.half_slice + uint32_t(bt) - 1) / uint32_t(bt);
+  w.lag = uint32_t(c.wave_lag < 1 ? 1 : (c.wave_lag > c.g.nt - 1 ? c.g.nt - 1 : c.wave_lag));
+  w.skip = c.wave_skip < 2u * w.nt * w.chunks ? c.wave_skip : 0u;
+  if constexpr (S == kQuat) {
+    if (mode == kHeatbathMode)
+      return ru ? launch_wave(update_pair_quat<R, kHeatbathMode, true>, bt, c, p, w)
+                : launch_wave(update_pair_quat<R, kHeatbathMode, false>, bt, c, p, w);
+    return ru ? launch_wave(update_pair_quat<R, kOverrelaxMode, true>, bt, c, p, w)
+              : launch_wave(update_pair_quat<R, kOverrelaxMode, false>, bt, c, p, w);
+  } else if constexpr (has_variants<R, N, S>()) {
+    if (occ) return launch_pair_mat<R, N, S, 1>(c, mode, ru, bt, p, w);
+    return launch_pair_mat<R, N, S, 0>(c, mode, ru, bt, p, w);
+  } else {
+    return launch_pair_mat<R, N, S, 0>(c, mode, ru, bt, p, w);
+  }
+}
+
 inline LinkParams make_link_params(const Ctx& c, int hot) {
   LinkParams p;
   p.links = c.links;
@@ -1588,6 +1793,7 @@ const Ops* ops_instance() {
       has_fused_reunit<R, N>() ? 1 : 0,
       has_group<R, N>() && S == kFull ? Group<R, N>::LPB : 0,
       &launch_pass<R, N, S>,
+      &launch_pair<R, N, S>,
       &launch_init<R, N, S>,
       &launch_reunit<R, N, S>,
       &launch_plaquette<R, N, S>,

@@ -44,6 +44,10 @@ struct DevState {
 
 constexpr int kMaxReduceBlocks = 1024;
 
+// Words of a lattice's wavefront synchronisation area before the per-t-slice
+// counters: wait timeouts, ticket.
+constexpr int kWaveSyncWords = 2;
+
 // Everything a launcher needs to enqueue work on one lattice.
 struct Ctx {
   char* links;          // 8 blocks (direction, parity)
@@ -58,7 +62,11 @@ struct Ctx {
   int block_threads;
   int reduce_blocks;
   int obs_stride, obs_offset;  // observable output: row stride and column (1, 0 for one lattice)
-  int variant;  // update-pass kernel variant (1: 6 blocks/SM bound, 2: two-row staple, 4: swap row-parallel / per-link kernel for Nc 4, 6)
+  int variant;  // update-pass kernel variant (1: 6 blocks/SM bound, 2: two-row staple, 4: swap row-parallel / per-link
+                // kernel for Nc 4, 6, 8: even and odd pass of a direction in one wavefront launch)
+  uint32_t* wave;  // kWaveSyncWords + Nt words of wavefront synchronisation
+  int wave_lag;    // t-slices the even units of a wavefront run ahead of the odd ones
+  uint32_t wave_skip;  // fault injection: leading units every wavefront launch leaves out (0 normally)
 };
 
 // One chain (lattice) of a batch, as the batched kernels read it.
@@ -104,6 +112,9 @@ struct Ops {
   int group_links_per_block;  // > 0: passes without re-unitarization use the row-parallel kernel
   cudaError_t (*pass)(const Ctx&, int mode, int mu, int parity, uint32_t step_offset, uint32_t reunit_mod,
                       uint32_t reunit_rem);
+  // both parities of direction mu in one wavefront launch (same results as the two passes)
+  cudaError_t (*pass_pair)(const Ctx&, int mode, int mu, uint32_t step_offset, uint32_t reunit_mod,
+                           uint32_t reunit_rem);
   cudaError_t (*init)(const Ctx&, int hot);
   cudaError_t (*reunit)(const Ctx&);
   cudaError_t (*plaquette)(const Ctx&, double* out, const uint32_t* slot, int cap);

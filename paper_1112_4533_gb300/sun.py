@@ -31,7 +31,7 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("storage", ctypes.c_int), ("reunit_every", ctypes.c_int),
                 ("block_threads", ctypes.c_int), ("stream", ctypes.c_void_p), ("device_buf", ctypes.c_void_p),
                 ("device_buf_bytes", ctypes.c_size_t), ("use_graphs", ctypes.c_int), ("variant", ctypes.c_int),
-                ("reunit_mode", ctypes.c_int)]
+                ("reunit_mode", ctypes.c_int), ("wave_lag", ctypes.c_int), ("wave_skip_units", ctypes.c_int)]
 
 
 class LatticeInfo(ctypes.Structure):
@@ -73,7 +73,14 @@ SIGNATURES = [
     ("sun_batch_create", ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int, _P, ctypes.c_int]),
     ("sun_batch_run", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D]),
     ("sun_batch_destroy", None, [_P]),
+    ("sun_autotune", ctypes.c_int, [ctypes.c_int, _I4, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.POINTER(Options), _D]),
+    ("sun_autotune_batch", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                          _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Options),
+                                          _D]),
 ]
+
+TUNE_STORAGE, TUNE_REUNIT_MODE, TUNE_TWO_ROW = 1, 2, 4
 
 
 def load_library(path=None):
@@ -107,7 +114,7 @@ def _dims(dims):
 
 
 def _options(precision=32, storage=0, reunit_every=1, block_threads=0, stream=None, device_buf=None,
-             device_buf_bytes=0, use_graphs=True, variant=0, reunit_mode=0):
+             device_buf_bytes=0, use_graphs=True, variant=0, reunit_mode=0, wave_lag=0, wave_skip_units=0):
     o = Options()
     load_library().sun_options_init(ctypes.byref(o))
     o.precision = int(precision)
@@ -120,7 +127,45 @@ def _options(precision=32, storage=0, reunit_every=1, block_threads=0, stream=No
     o.use_graphs = 1 if use_graphs else 0
     o.variant = int(variant)
     o.reunit_mode = int(reunit_mode)
+    o.wave_lag = int(wave_lag)
+    o.wave_skip_units = int(wave_skip_units)
     return o
+
+
+def _tuned(o, ms):
+    return {"storage": o.storage, "block_threads": o.block_threads, "variant": o.variant,
+            "reunit_mode": o.reunit_mode, "ms_per_sweep": ms.value}
+
+
+def autotune(nc, dims, beta, n_heatbath=1, n_overrelax=4, precision=32, storage=0, reunit_mode=0,
+             tune_storage=True, tune_reunit_mode=False, two_row=False, use_graphs=True):
+    """Measured kernel configuration for one lattice (sun_autotune): a dict of
+    Lattice keyword arguments (storage, block_threads, variant, reunit_mode)
+    plus ms_per_sweep of the winner."""
+    flags = (TUNE_STORAGE if tune_storage else 0) | (TUNE_REUNIT_MODE if tune_reunit_mode else 0) | \
+        (TUNE_TWO_ROW if two_row else 0)
+    o = _options(precision, storage, use_graphs=use_graphs, reunit_mode=reunit_mode)
+    ms = ctypes.c_double(0.0)
+    _check(load_library().sun_autotune(int(nc), _dims(dims), float(beta), int(n_heatbath), int(n_overrelax), flags,
+                                       ctypes.byref(o), ctypes.byref(ms)))
+    return _tuned(o, ms)
+
+
+def autotune_batch(chains, n_heatbath=1, n_overrelax=4, precision=32, storage=0, reunit_mode=0,
+                   tune_storage=True, tune_reunit_mode=False, two_row=False, use_graphs=True):
+    """Measured configuration shared by a batch (sun_autotune_batch); chains is a
+    list of (nc, dims, beta).  Returns the dict of autotune()."""
+    n = len(chains)
+    ncs = (ctypes.c_int * n)(*[int(c[0]) for c in chains])
+    dims = (ctypes.c_int * (4 * n))(*[int(d) for c in chains for d in c[1]])
+    betas = np.array([float(c[2]) for c in chains], dtype=np.float64)
+    flags = (TUNE_STORAGE if tune_storage else 0) | (TUNE_REUNIT_MODE if tune_reunit_mode else 0) | \
+        (TUNE_TWO_ROW if two_row else 0)
+    o = _options(precision, storage, use_graphs=use_graphs, reunit_mode=reunit_mode)
+    ms = ctypes.c_double(0.0)
+    _check(load_library().sun_autotune_batch(n, ncs, dims, _dptr(betas), int(n_heatbath), int(n_overrelax), flags,
+                                             ctypes.byref(o), ctypes.byref(ms)))
+    return _tuned(o, ms)
 
 
 def footprint_bytes(nc, dims, precision=32, storage=0):
@@ -141,7 +186,8 @@ class Lattice:
     """
 
     def __init__(self, nc, dims, beta, hot_start=False, seed=1, precision=32, storage=0, reunit_every=1,
-                 block_threads=0, stream=None, use_graphs=True, device=None, variant=0, reunit_mode=0):
+                 block_threads=0, stream=None, use_graphs=True, device=None, variant=0, reunit_mode=0,
+                 wave_lag=0, wave_skip_units=0):
         import torch  # device memory and streams only
 
         self.nc = int(nc)
@@ -162,7 +208,8 @@ class Lattice:
         base = self._buf.data_ptr()
         aligned = (base + 255) // 256 * 256
         o = _options(precision, storage, reunit_every, block_threads, ctypes.c_void_p(self.stream.cuda_stream),
-                     ctypes.c_void_p(aligned), nbytes, use_graphs, variant, reunit_mode)
+                     ctypes.c_void_p(aligned), nbytes, use_graphs, variant, reunit_mode, wave_lag,
+                     wave_skip_units)
         # the tensor's memory must be usable on our stream
         self.stream.wait_stream(torch.cuda.current_stream(dev))
         h = ctypes.c_void_p()

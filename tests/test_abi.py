@@ -103,3 +103,26 @@ def test_negative_beta_rejected(lib):
     o = sun._options()
     h = ctypes.c_void_p()
     assert lib.sun_lattice_create(ctypes.byref(h), 3, _dims((4, 4, 4, 4)), -1.0, 0, 1, ctypes.byref(o)) == 1
+
+
+def test_autotune_rejects_invalid_requests_on_the_host(lib):
+    from paper_1112_4533_gb300 import sun
+    ms = ctypes.c_double()
+    o = sun._options()
+    d = _dims((4, 4, 4, 4))
+    # a sweep without steps, unknown flags, caller memory: refused before any device work
+    assert lib.sun_autotune(3, d, 6.0, 0, 0, 0, ctypes.byref(o), ctypes.byref(ms)) == 1
+    assert lib.sun_autotune(3, d, 6.0, 1, 1, 64, ctypes.byref(o), ctypes.byref(ms)) == 1
+    o.device_buf = ctypes.c_void_p(4096)
+    assert lib.sun_autotune(3, d, 6.0, 1, 1, 0, ctypes.byref(o), ctypes.byref(ms)) == 1
+    assert lib.sun_autotune(3, d, 6.0, 1, 1, 0, None, ctypes.byref(ms)) == 1
+    assert lib.sun_autotune_batch(0, None, None, None, 1, 1, 0, ctypes.byref(sun._options()), None) == 1
+
+
+def test_wavefront_options_validated_on_the_host(lib):
+    from paper_1112_4533_gb300 import sun
+    h = ctypes.c_void_p()
+    for field, bad in (("variant", 16), ("wave_lag", -1), ("wave_skip_units", -2)):
+        o = sun._options()
+        setattr(o, field, bad)
+        assert lib.sun_lattice_create(ctypes.byref(h), 3, _dims((4, 4, 4, 4)), 6.0, 0, 1, ctypes.byref(o)) == 1
