@@ -193,6 +193,94 @@ def oracle_sample(target_seconds=12.0, threads=None, max_slices=24):
     return r, cores, desc
 
 
+def oracle_leg(L, n_doubles, target_seconds=12.0, max_slices=24):
+    """The CPU baseline on the GPU's own configuration, with the agreement of
+    the two stated: the FP64 oracle measures the plaquette and Polyakov loop of
+    the configuration the GPU holds after the timed sweeps, then repeats one
+    heatbath pass and one overrelaxation pass of the GPU (same input, same
+    Philox counters) on the first time slices, timing each (rates combined 1:5
+    as in a sweep).  Returns the cpu_baseline dict with an "agreement" entry."""
+    import numpy as np
+    import torch
+    import oracle as orc
+    import paper_1112_4533_gb300 as sun
+
+    cores = orc.set_threads(os.cpu_count() or 1)
+    nx, ny, nz, nt = DIMS
+    shape = (4, nt, nz, ny, nx, NC, NC)
+    a = torch.empty(n_doubles, dtype=torch.float64).pin_memory()
+    b = torch.empty(n_doubles, dtype=torch.float64).pin_memory()
+    A = a.numpy().view(np.complex128).reshape(shape)
+    B = b.numpy().view(np.complex128).reshape(shape)
+    L.export_links_raw(a.data_ptr(), n_doubles)
+    p_gpu = L.plaquette()
+    l_gpu = L.polyakov_loop()
+    t0 = time.perf_counter()
+    p_orc = orc.plaquette(A)
+    t_plaq = time.perf_counter() - t0
+    l_orc = orc.polyakov(A)
+    l_orc = complex(l_orc[0], l_orc[1]) if isinstance(l_orc, tuple) else complex(l_orc)
+    step = L.heatbath_step
+    n_slab = max(1, min(max_slices, nt - 2))
+    per_pass = nx * ny * nz // 2 * n_slab
+
+    def slab_diff(X, Y):
+        d = np.abs(X[:, :n_slab] - Y[:, :n_slab]).reshape(4, n_slab, -1, NC * NC).max(axis=-1)
+        return d
+
+    # heatbath pass (mu 1, even) from A: GPU on the whole lattice, oracle on the slab
+    L.update_pass(sun.HEATBATH, 1, 0)
+    L.export_links_raw(b.data_ptr(), n_doubles)
+    n_hb, t_hb = 0, 0.0
+    t0 = time.perf_counter()
+    orc.update_pass(A, BETA, orc.HEATBATH, 1, 0, step, 1, 0, n_slab)
+    t_hb += time.perf_counter() - t0
+    n_hb += per_pass
+    d = slab_diff(A, B)
+    flips = int((d > 1e-5).sum())
+    hb_err = float(d[d <= 1e-5].max())
+    # overrelaxation pass (mu 2, odd) from the GPU's post-heatbath state B
+    L.update_pass(sun.OVERRELAX, 2, 1)
+    L.export_links_raw(a.data_ptr(), n_doubles)
+    t0 = time.perf_counter()
+    orc.update_pass(B, BETA, orc.OVERRELAX, 2, 1, step, 1, 0, n_slab)
+    t_or = time.perf_counter() - t0
+    n_or = per_pass
+    or_err = float(slab_diff(A, B).max())
+    # more passes of each kind on the slab for a steadier rate (results not compared)
+    k = 0
+    while t_hb + t_or < target_seconds and k < 64:
+        mu, par = (k // 2) % 4, k % 2
+        t0 = time.perf_counter()
+        orc.update_pass(B, BETA, orc.HEATBATH if k % 2 == 0 else orc.OVERRELAX, mu, par, step + 1, 1, 0, n_slab)
+        if k % 2 == 0:
+            t_hb += time.perf_counter() - t0
+            n_hb += per_pass
+        else:
+            t_or += time.perf_counter() - t0
+            n_or += per_pass
+        k += 1
+    r_hb, r_or = n_hb / t_hb, n_or / t_or
+    r = (N_HB + N_OR) / (N_HB / r_hb + N_OR / r_or)
+    desc = (f"FP64 oracle on the GPU's configuration after the timed sweeps: heatbath and overrelaxation passes "
+            f"over time slices [0,{n_slab}) of the 48^3x96 lattice ({per_pass} link updates per pass), "
+            f"{n_hb} heatbath updates in {t_hb:.1f} s, {n_or} overrelaxation updates in {t_or:.1f} s, rates "
+            f"combined 1:5 as in a sweep; plaquette of the whole lattice in {t_plaq:.1f} s")
+    agreement = {
+        "plaquette": {"gpu": p_gpu, "oracle": p_orc, "abs_err": abs(p_gpu - p_orc)},
+        "polyakov": {"gpu": [l_gpu.real, l_gpu.imag], "oracle": [l_orc.real, l_orc.imag],
+                     "abs_err": abs(l_gpu - l_orc)},
+        "overrelaxation_pass": {"links": 4 * per_pass, "max_abs_err": or_err, "bound": 1e-5},
+        "heatbath_pass": {"links": 4 * per_pass, "max_abs_err_where_branches_agree": hb_err,
+                          "branch_flips": flips, "bound": "1e-5, flips <= 1e-6 of updates"},
+        "note": "one pass from the same FP64 input; links of all four directions on the slab compared "
+                "(only direction 1 / 2 changes)",
+    }
+    del A, B, a, b
+    return {"value": r, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": desc,
+            "plaquette_s": t_plaq, "agreement": agreement}
+
+
 # ---------------------------------------------------------------- GPU arm ----
 
 def dist_init(n_gpus):
@@ -364,8 +452,7 @@ def gpu_arm(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        rate, cores, desc = oracle_sample(args.cpu_seconds)
-        cpu = {"value": rate, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": desc}
+        cpu = oracle_leg(L, 8 * NC * NC * V, args.cpu_seconds)
 
     L.close()
     launches_per_sweep = (N_HB + N_OR) * 8 + 4  # passes, reunitarization, plaquette, Polyakov, counter

@@ -70,12 +70,25 @@ __device__ __forceinline__ void apply_rows(Mat<R, N>& m, int i, int j, const Qua
 // ---------------------------------------------------------------------------
 // FP64 re-unitarization of one matrix (Sec. 2).
 // ---------------------------------------------------------------------------
+// 1/sqrt(s).  Rows of links stored in FP32 are within ~1e-6 of unit norm, and
+// there the binomial series (1 + d)^(-1/2) = 1 - d/2 + 3 d^2/8 - 5 d^3/16 + ...
+// with d = s - 1, cut after d^3, is exact to FP64 rounding: the first omitted
+// term, 35 d^4 / 128, is below 4e-18 for |d| < 2^-14.  Other rows use rsqrt().
+__device__ __forceinline__ double rsqrt_near_one(double s) {
+  const double d = s - 1.0;
+  if (fabs(d) < 0x1p-14) return fma(fma(fma(-0.3125, d, 0.375), d, -0.5), d, 1.0);
+  return rsqrt(s);
+}
+
 template <int N>
 __device__ __forceinline__ void normalise_row(Mat<double, N>& m, int r) {
   double s = 0.0;
 #pragma unroll
-  for (int c = 0; c < N; ++c) s += m.e[r][c].re * m.e[r][c].re + m.e[r][c].im * m.e[r][c].im;
-  const double inv = rsqrt(s);
+  for (int c = 0; c < N; ++c) {
+    s = fma(m.e[r][c].re, m.e[r][c].re, s);
+    s = fma(m.e[r][c].im, m.e[r][c].im, s);
+  }
+  const double inv = rsqrt_near_one(s);
 #pragma unroll
   for (int c = 0; c < N; ++c) {
     m.e[r][c].re *= inv;
@@ -147,11 +160,12 @@ __device__ __forceinline__ void reunit_d(Mat<double, N>& m) {
         Cpx<double> pr = {0.0, 0.0};
 #pragma unroll
         for (int c = 0; c < N; ++c) ccfma(pr, m.e[q][c], m.e[r][c]);
+        // row r -= pr * row q
 #pragma unroll
         for (int c = 0; c < N; ++c) {
-          const Cpx<double> t = cmul(pr, m.e[q][c]);
-          m.e[r][c].re -= t.re;
-          m.e[r][c].im -= t.im;
+          const Cpx<double> a = m.e[q][c];
+          m.e[r][c].re = fma(pr.im, a.im, fma(-pr.re, a.re, m.e[r][c].re));
+          m.e[r][c].im = fma(-pr.im, a.re, fma(-pr.re, a.im, m.e[r][c].im));
         }
       }
       normalise_row<N>(m, r);
@@ -795,7 +809,7 @@ __device__ __forceinline__ void quat_pass_body(const PassParams& p, int par, int
   if constexpr (REUNIT) {
     if (reunit_selected(p, h)) {
       const double a0 = u.a0, a1 = u.a1, a2 = u.a2, a3 = u.a3;
-      const double inv = rsqrt(a0 * a0 + a3 * a3 + a2 * a2 + a1 * a1);
+      const double inv = rsqrt_near_one(fma(a1, a1, fma(a2, a2, fma(a3, a3, a0 * a0))));
       u = Quat<R>{R(a0 * inv), R(a1 * inv), R(a2 * inv), R(a3 * inv)};
     }
   }
@@ -955,7 +969,7 @@ __global__ void __launch_bounds__(256) reunit_kernel(const LinkParams p) {
   if constexpr (S == kQuat) {
     const Quat<R> q = load_quat<R, kLoadPlain>(blk, p.g.Vh, h);
     const double a0 = q.a0, a1 = q.a1, a2 = q.a2, a3 = q.a3;
-    const double inv = rsqrt(a0 * a0 + a3 * a3 + a2 * a2 + a1 * a1);
+    const double inv = rsqrt_near_one(fma(a1, a1, fma(a2, a2, fma(a3, a3, a0 * a0))));
     store_quat<R>(blk, p.g.Vh, h, Quat<R>{R(a0 * inv), R(a1 * inv), R(a2 * inv), R(a3 * inv)});
   } else {
     Mat<double, N> m = mat_cast<R, double, N>(load_mat<R, N, S, kLoadPlain>(blk, p.g.Vh, h));
@@ -1288,7 +1302,7 @@ __global__ void __launch_bounds__(128) reunit_batch(const BatchParams bp) {
   if constexpr (S == kQuat) {
     const Quat<R> q = load_quat<R, kLoadPlain>(blk, sp.g.Vh, h);
     const double a0 = q.a0, a1 = q.a1, a2 = q.a2, a3 = q.a3;
-    const double inv = rsqrt(a0 * a0 + a3 * a3 + a2 * a2 + a1 * a1);
+    const double inv = rsqrt_near_one(fma(a1, a1, fma(a2, a2, fma(a3, a3, a0 * a0))));
     store_quat<R>(blk, sp.g.Vh, h, Quat<R>{R(a0 * inv), R(a1 * inv), R(a2 * inv), R(a3 * inv)});
   } else {
     Mat<double, N> m = mat_cast<R, double, N>(load_mat<R, N, S, kLoadPlain>(blk, sp.g.Vh, h));
