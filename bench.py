@@ -573,7 +573,8 @@ def serving_arm(args):
     budget = int(args.budget_gb * (1 << 30))
     warm = serve.poisson_trace(4, rate=50.0, seed=99, Ls=(8,), sweeps=(2, 3))
     serve.Server(budget).run(warm)  # load kernels
-    srv = serve.Server(budget, sweeps_per_tick=args.sweeps_per_tick, work_cap_ms=args.work_cap_ms)
+    srv = serve.Server(budget, sweeps_per_tick=args.sweeps_per_tick or None, work_cap_ms=args.work_cap_ms,
+                       tick_ms=args.tick_ms, policy=args.policy)
     t0 = time.perf_counter()
     out = srv.run(trace)
     wall = time.perf_counter() - t0
@@ -586,8 +587,8 @@ def serving_arm(args):
            "dtype": "f32", "data": "synthetic Poisson trace (seed 7)",
            "config": {"workload": f"{args.requests} requests, Poisson mean 20/s, Nc in {{2,3,4,6}}, L in "
                                   "{8,12,16,20,24}, 20..200 sweeps of 1 heatbath + 4 overrelaxation, FP32",
-                      "hbm_budget_gb": args.budget_gb, "sweeps_per_tick": args.sweeps_per_tick,
-                      "work_cap_ms": args.work_cap_ms},
+                      "hbm_budget_gb": args.budget_gb, "max_sweeps_per_tick": args.sweeps_per_tick or None,
+                      "tick_ms": args.tick_ms, "work_cap_ms": args.work_cap_ms, "policy": args.policy},
            "p99_s": st["p99_s"], "mean_s": st["mean_s"], "completed": st["completed"],
            "throughput": {"requests_per_s": len(trace) / wall, "link_updates_per_s": upd / wall},
            "plain": {"p50_s": pst["p50_s"], "p99_s": pst["p99_s"], "mean_s": pst["mean_s"],
@@ -630,7 +631,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--storage", type=int, default=12, choices=[12, 18])
     ap.add_argument("--variant", type=int, default=1, choices=range(16),
-                    help="update-kernel variant bits: 1 = 6 blocks/SM register bound, 2 = two-row staple")
+                    help="update-kernel variant bits: 1 = 5 blocks/SM register bound, 2 = two-row staple")
     ap.add_argument("--reunit-mode", type=int, default=1, choices=[0, 1, 2])
     ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -642,7 +643,9 @@ def main():
     ap.add_argument("--workload", choices=["single", "batched", "serving"], default="single")
     ap.add_argument("--requests", type=int, default=80)
     ap.add_argument("--budget-gb", type=float, default=64.0)
-    ap.add_argument("--sweeps-per-tick", type=int, default=8)
+    ap.add_argument("--sweeps-per-tick", type=int, default=0, help="cap on sweeps per serving tick (0 = none)")
+    ap.add_argument("--tick-ms", type=float, default=40.0, help="predicted GPU time a serving tick aims at")
+    ap.add_argument("--policy", choices=["srpt", "fifo"], default="srpt")
     ap.add_argument("--work-cap-ms", type=float, default=3.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -75,7 +75,7 @@ enum { SUN_HEATBATH = 0, SUN_OVERRELAX = 1 };
  *  use_graphs    sun_run captures one sweep as a CUDA graph and replays it (default 1).
  *  variant       update-pass kernel variant, bit flags (default 0); results do not
  *                depend on bits 1 and 4:
- *                1 = (SU(3) FP32) bound the registers for 6 resident 128-thread
+ *                1 = (SU(3) FP32) bound the registers for 5 resident 128-thread
  *                blocks per SM;
  *                2 = (SU(3) FP32 two-row storage) multiply out rows 0 and 1 of each
  *                staple term only and take its third row as conj(row0 x row1),

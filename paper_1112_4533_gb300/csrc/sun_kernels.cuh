@@ -12,6 +12,10 @@
 namespace sun {
 
 constexpr int kMaxBlockThreads = 256;
+// resident 128-thread blocks per SM the register-bounded kernels (variant bit 1)
+// are compiled for: 5 measured fastest among 5..8 for the SU(3) FP32 passes on
+// GB300 (more warps cost more spills than they hide latency)
+constexpr int kOccBlocks = 5;
 constexpr int kHeatbathMode = 0;
 constexpr int kOverrelaxMode = 1;
 
@@ -397,7 +401,7 @@ __device__ __forceinline__ void pass_body(const PassParams& p, int par, int64_t 
   store_mat<R, N, S>(ublk, g.Vh, h, u);
 }
 
-// VAR bit 0: at most 128 threads per block and registers for 6 blocks per SM;
+// VAR bit 0: at most 128 threads per block and registers for kOccBlocks blocks per SM;
 // VAR bit 1: two-row staple products (SU(3) two-row storage only).
 // REUNIT: the FP64 re-unitarization of selected links is compiled in (passes that
 // re-unitarize use this instantiation; the others carry no FP64 code).
@@ -409,7 +413,7 @@ __global__ void __launch_bounds__(kMaxBlockThreads) update_pass_mat(const PassPa
 }
 
 template <class R, int N, int S, int MODE, int VAR, bool REUNIT>
-__global__ void __launch_bounds__(128, 6) update_pass_mat_occ(const PassParams p) {
+__global__ void __launch_bounds__(128, kOccBlocks) update_pass_mat_occ(const PassParams p) {
   const int64_t h = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (h >= p.g.Vh) return;
   pass_body<R, N, S, MODE, (VAR & 2) != 0, REUNIT>(p, p.parity, h);
@@ -942,7 +946,7 @@ __global__ void __launch_bounds__(kMaxBlockThreads) update_pair_mat(const PassPa
 }
 
 template <class R, int N, int S, int MODE, int VAR, bool REUNIT>
-__global__ void __launch_bounds__(128, 6) update_pair_mat_occ(const PassParams p, const WaveParams w) {
+__global__ void __launch_bounds__(128, kOccBlocks) update_pair_mat_occ(const PassParams p, const WaveParams w) {
   wavefront<R, N, S, MODE, (VAR & 2) != 0, REUNIT, false>(p, w);
 }
 
@@ -1239,7 +1243,7 @@ __global__ void __launch_bounds__(kMaxBlockThreads)
 }
 
 template <class R, int N, int S, int MODE, int VAR, bool REUNIT>
-__global__ void __launch_bounds__(128, 6)
+__global__ void __launch_bounds__(128, kOccBlocks)
     update_pass_batch_occ(const BatchParams bp, int mu, int parity, uint32_t step_offset, uint32_t rmod,
                           uint32_t rrem) {
   batch_pass_body<R, N, S, MODE, VAR, REUNIT>(bp, mu, parity, step_offset, rmod, rrem);

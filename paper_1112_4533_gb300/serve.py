@@ -5,10 +5,11 @@ steps, re-unitarization) of an SU(Nc) chain on an L^4 lattice from a Haar
 start, and gets back its plaquette and Polyakov-loop history.  The server keeps
 every admitted chain's links and random state (seed, heatbath counter) resident
 on the GPU, admits waiting requests in arrival order as soon as their device
-footprint fits the memory budget, and advances all admitted chains together:
-each tick is one batched run (sun_batch_run) over every active chain, chains of
-different Nc on their own streams.  Requests that arrive while others are on
-the GPU join at the next tick; finished chains leave and free their memory.
+footprint fits the memory budget, and advances chains together: each tick is
+one batched run (sun_batch_run) over the chains the scheduling policy picks,
+chains of different Nc on their own streams.  Requests that arrive while others
+are on the GPU join at the next tick; finished chains leave and free their
+memory.  A chain's results do not depend on which ticks and batches it ran in.
 
 The plain path (serve_plain) runs the same trace one request at a time, each
 chain alone (sun_run), in arrival order.
@@ -83,23 +84,48 @@ def sweep_cost_ms(req):
 class Server:
     """Continuous batching over a device-memory budget (bytes).
 
-    Waiting requests are admitted in arrival order while their footprint fits
-    the budget and, when work_cap_ms is set, while the predicted time of one
-    sweep of all admitted chains stays below it (an empty GPU always takes the
-    next request): small chains share the GPU, a large one does not stretch the
-    latency of everything admitted with it."""
+    Admission: waiting requests are admitted in arrival order as soon as their
+    footprint fits the budget; an admitted chain keeps its links and random
+    state resident until it has all its sweeps.
+    Each tick: the server picks which resident chains to advance and runs them
+    as one batch (sun_batch_run) for k sweeps.  policy "srpt" takes chains in
+    order of least remaining work (remaining sweeps x predicted sweep time),
+    "fifo" in admission order; both add chains while the predicted time of one
+    sweep of the selection stays within work_cap_ms (the first chain always
+    runs).  k is as many sweeps as fill about tick_ms of predicted GPU time, at
+    most the fewest remaining sweeps of the selection.  Under srpt a large
+    request no longer holds small ones behind it: they run beside it or
+    between its ticks, and leave as soon as they are done."""
 
-    def __init__(self, hbm_budget, n_overrelax=4, sweeps_per_tick=8, precision=32, use_graphs=True,
-                 work_cap_ms=None, clock=time.perf_counter):
+    def __init__(self, hbm_budget, n_overrelax=4, sweeps_per_tick=None, precision=32, use_graphs=True,
+                 work_cap_ms=3.0, tick_ms=40.0, policy="srpt", clock=time.perf_counter):
+        if policy not in ("srpt", "fifo"):
+            raise ValueError("policy must be 'srpt' or 'fifo'")
         self.work_cap = work_cap_ms
         self.budget = int(hbm_budget)
         self.n_or = int(n_overrelax)
-        self.k = int(sweeps_per_tick)
+        self.max_k = None if sweeps_per_tick is None else int(sweeps_per_tick)
+        self.tick_ms = float(tick_ms)
+        self.policy = policy
         self.precision = precision
         self.use_graphs = use_graphs
         self.clock = clock
         self.ticks = 0
         self.link_updates = 0
+
+    def _select(self, active):
+        if self.policy == "srpt":
+            order = sorted(active, key=lambda a: ((a[0].n_sweeps - a[2]) * sweep_cost_ms(a[0]), a[0].arrival))
+        else:
+            order = list(active)
+        sel, cost = [], 0.0
+        for a in order:
+            c = sweep_cost_ms(a[0])
+            if sel and self.work_cap is not None and cost + c > self.work_cap:
+                continue
+            sel.append(a)
+            cost += c
+        return sel, cost
 
     def run(self, trace: List[Request]):
         """Serve the trace in real time; returns the requests with their results."""
@@ -110,17 +136,10 @@ class Server:
         batch = None
         members = None
         t0 = self.clock()
-
-        def work_fits(r):
-            if self.work_cap is None or not active:
-                return True
-            return sum(sweep_cost_ms(a[0]) for a in active) + sweep_cost_ms(r) <= self.work_cap
-
         while pending or active:
             now = self.clock() - t0
             # admit in arrival order while the head of the queue fits the budget
-            while pending and pending[0].arrival <= now and used + footprint(pending[0], self.precision) <= self.budget \
-                    and work_fits(pending[0]):
+            while pending and pending[0].arrival <= now and used + footprint(pending[0], self.precision) <= self.budget:
                 r = pending.pop(0)
                 fp = footprint(r, self.precision)
                 lat = sun.Lattice(r.nc, r.dims, r.beta, hot_start=True, seed=r.seed, precision=self.precision)
@@ -132,21 +151,25 @@ class Server:
                     raise RuntimeError(f"request {pending[0].rid} does not fit the memory budget")
                 time.sleep(min(pending[0].arrival - now, 0.05))
                 continue
-            ids = tuple(id(a[1]) for a in active)
+            sel, cost = self._select(active)
+            ids = tuple(id(a[1]) for a in sel)
             if ids != members:
                 if batch is not None:
                     batch.close()
-                batch = sun.Batch([a[1] for a in active], use_graphs=self.use_graphs)
+                batch = sun.Batch([a[1] for a in sel], use_graphs=self.use_graphs)
                 members = ids
-            k = min(self.k, min(a[0].n_sweeps - a[2] for a in active))
+            k = min(a[0].n_sweeps - a[2] for a in sel)
+            k = min(k, max(1, int(self.tick_ms / max(cost, 1e-6))))
+            if self.max_k is not None:
+                k = min(k, self.max_k)
             plaq, poly = batch.run(k, 1, self.n_or)
             self.ticks += 1
-            for j, a in enumerate(active):
+            for j, a in enumerate(sel):
                 a[2] += k
                 a[3].extend(plaq[:, j].tolist())
                 a[4].extend(poly[:, j].tolist())
                 self.link_updates += k * (1 + self.n_or) * 4 * int(np.prod(a[0].dims))
-            done = [a for a in active if a[2] >= a[0].n_sweeps]
+            done = [a for a in sel if a[2] >= a[0].n_sweeps]
             if done:
                 t = self.clock() - t0
                 for a in done:
