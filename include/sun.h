@@ -206,6 +206,49 @@ typedef struct {
 sun_status sun_get_info(const sun_lattice* lat, sun_lattice_info* info);
 
 /* ---------------------------------------------------------------------------
+ * Configuration files.  The paper stores the generated configurations (Sec. 3);
+ * this format also carries the chain's state, so that a saved lattice resumes
+ * bitwise: links, beta, seed, heatbath step counter and sweep count.
+ *
+ * Layout (little-endian): a 128-byte header, then the payload.
+ *   header: char magic[8] = "SUNCFG01", then sun_config_header as laid out below
+ *   payload: every link in canonical order (mu, t, z, y, x), for each the rows
+ *   0 .. rows-1 of the matrix as (re, im) pairs, in the lattice's precision
+ *   (float or double); rows = storage / (2 Nc): the rows the storage format
+ *   keeps (SU(2) quaternion storage: row 0 = (a0 + i a3, a2 + i a1); SU(3)
+ *   two-row: rows 0, 1; full storage: all rows).  FP32 links are stored exactly.
+ *   checksum: FNV-1a (64-bit offset basis and prime) over the payload read as
+ *   little-endian 64-bit words (the payload is a multiple of 8 bytes).
+ */
+typedef struct {
+  uint32_t version;        /* 1 */
+  int32_t nc, precision, storage;
+  int32_t dims[4];
+  double beta;
+  uint64_t seed;
+  uint64_t heatbath_step;
+  uint64_t sweeps_done;    /* sets the re-unitarization cadence (reunit_every) */
+  uint64_t payload_bytes;  /* 4V * rows * Nc * 2 * (precision / 8) */
+  uint64_t checksum;
+  uint8_t reserved[40];
+} sun_config_header;       /* 120 bytes, stored right after the 8-byte magic */
+
+/* Write the lattice and its chain state to path (created or truncated).
+ * Streams through the lattice's staging buffer.  Syncs. */
+sun_status sun_save_config(sun_lattice* lat, const char* path);
+
+/* Read a file written by sun_save_config into a lattice of the same nc, dims,
+ * precision and storage (SUN_ERR_ARG otherwise): links, beta, seed, heatbath
+ * step and sweep count.  The whole payload is read and checksummed before the
+ * lattice is touched; a mismatch returns SUN_ERR_ARG with the lattice
+ * unchanged.  Syncs. */
+sun_status sun_load_config(sun_lattice* lat, const char* path);
+
+/* Read and check a file's header; with verify != 0 also read the payload and
+ * check its size and checksum.  Host only: needs no GPU. */
+sun_status sun_read_config_header(const char* path, int verify, sun_config_header* out);
+
+/* ---------------------------------------------------------------------------
  * Batches: many independent chains swept together.
  * A batch references existing lattices (they must outlive it) of possibly
  * different Nc, extents, beta and seed.  Lattices with the same (Nc, storage,

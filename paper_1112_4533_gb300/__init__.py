@@ -5,7 +5,7 @@ Chessboard heatbath / overrelaxation sweep of Cardoso & Bicudo,
 (arXiv:1112.4533), behind the C ABI of include/sun.h (libsun.so).
 """
 from .sun import (HEATBATH, OVERRELAX, Batch, Lattice, SunError, autotune, autotune_batch,  # noqa: F401
-                  footprint_bytes, lattice_create, load_library)
+                  footprint_bytes, lattice_create, load_library, read_config_header)
 
 __all__ = ["HEATBATH", "OVERRELAX", "Batch", "Lattice", "SunError", "autotune", "autotune_batch", "footprint_bytes",
-           "lattice_create", "load_library"]
+           "lattice_create", "load_library", "read_config_header"]

@@ -47,6 +47,13 @@ _lib = None
 _P = ctypes.c_void_p
 _I4 = ctypes.POINTER(ctypes.c_int)
 _D = ctypes.POINTER(ctypes.c_double)
+class ConfigHeader(ctypes.Structure):
+    _fields_ = [("version", ctypes.c_uint32), ("nc", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("storage", ctypes.c_int32), ("dims", ctypes.c_int32 * 4), ("beta", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("heatbath_step", ctypes.c_uint64), ("sweeps_done", ctypes.c_uint64),
+                ("payload_bytes", ctypes.c_uint64), ("checksum", ctypes.c_uint64), ("reserved", ctypes.c_uint8 * 40)]
+
+
 SIGNATURES = [
     ("sun_abi_version", ctypes.c_int, []),
     ("sun_options_init", None, [ctypes.POINTER(Options)]),
@@ -73,6 +80,9 @@ SIGNATURES = [
     ("sun_batch_create", ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int, _P, ctypes.c_int]),
     ("sun_batch_run", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D]),
     ("sun_batch_destroy", None, [_P]),
+    ("sun_save_config", ctypes.c_int, [_P, ctypes.c_char_p]),
+    ("sun_load_config", ctypes.c_int, [_P, ctypes.c_char_p]),
+    ("sun_read_config_header", ctypes.c_int, [ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(ConfigHeader)]),
     ("sun_autotune", ctypes.c_int, [ctypes.c_int, _I4, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                     ctypes.POINTER(Options), _D]),
     ("sun_autotune_batch", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -166,6 +176,16 @@ def autotune_batch(chains, n_heatbath=1, n_overrelax=4, precision=32, storage=0,
     _check(load_library().sun_autotune_batch(n, ncs, dims, _dptr(betas), int(n_heatbath), int(n_overrelax), flags,
                                              ctypes.byref(o), ctypes.byref(ms)))
     return _tuned(o, ms)
+
+
+def read_config_header(path, verify=True):
+    """Header of a configuration file (sun_read_config_header) as a dict; with
+    verify the payload size and checksum are checked too.  Needs no GPU."""
+    h = ConfigHeader()
+    _check(load_library().sun_read_config_header(os.fsencode(path), int(bool(verify)), ctypes.byref(h)))
+    return {"version": h.version, "nc": h.nc, "precision": h.precision, "storage": h.storage,
+            "dims": tuple(h.dims), "beta": h.beta, "seed": h.seed, "heatbath_step": h.heatbath_step,
+            "sweeps_done": h.sweeps_done, "payload_bytes": h.payload_bytes, "checksum": h.checksum}
 
 
 def footprint_bytes(nc, dims, precision=32, storage=0):
@@ -314,6 +334,14 @@ class Lattice:
     @heatbath_step.setter
     def heatbath_step(self, step):
         _check(self._lib.sun_set_heatbath_step(self.handle, int(step)))
+
+    def save(self, path):
+        """Write links and chain state to a configuration file (sun_save_config)."""
+        _check(self._lib.sun_save_config(self.handle, os.fsencode(path)))
+
+    def load(self, path):
+        """Resume the chain stored in a configuration file (sun_load_config)."""
+        _check(self._lib.sun_load_config(self.handle, os.fsencode(path)))
 
     def set_beta(self, beta):
         _check(self._lib.sun_set_beta(self.handle, float(beta)))

@@ -1,0 +1,81 @@
+"""GPU tests of configuration files (sun_save_config / sun_load_config): a
+chain saved mid-run and loaded into a fresh lattice (created with another seed,
+beta and a cold start) continues bitwise as the uninterrupted chain, for every
+storage format; the file's links are the lattice's exported links; mismatched
+or damaged files are refused and leave the lattice unchanged."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sunlib():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1112_4533_gb300 import build as b
+    b.build()
+    import paper_1112_4533_gb300 as p
+    p.load_library()
+    return p
+
+
+CASES = [(2, 4, 32), (2, 8, 64), (3, 12, 32), (3, 18, 32), (3, 12, 64), (4, 32, 32), (6, 72, 32)]
+
+
+def beta_for(nc):
+    return 2.3 if nc == 2 else (6.0 if nc == 3 else 0.7 * nc * nc)
+
+
+@pytest.mark.parametrize("nc,st,prec", CASES)
+def test_save_load_resumes_bitwise(sunlib, tmp_path, nc, st, prec):
+    dims = (4, 4, 6, 4)
+    kw = dict(storage=st, precision=prec, reunit_every=2)
+    with sunlib.Lattice(nc, dims, beta_for(nc), hot_start=True, seed=21, **kw) as A:
+        ref_p, ref_l = A.run(5, 1, 2)
+        ref = A.export_links()
+    path = tmp_path / "chain.cfg"
+    with sunlib.Lattice(nc, dims, beta_for(nc), hot_start=True, seed=21, **kw) as B:
+        B.run(3, 1, 2)  # an odd sweep count: the re-unitarization cadence must resume too
+        B.save(path)
+        saved = B.export_links()
+    h = sunlib.read_config_header(path)
+    assert (h["nc"], h["storage"], h["precision"], h["seed"], h["heatbath_step"], h["sweeps_done"]) == \
+        (nc, st, prec, 21, 3, 3)
+    with sunlib.Lattice(nc, dims, 1.0, hot_start=False, seed=99, **kw) as C:
+        C.load(path)
+        assert np.array_equal(C.export_links(), saved)
+        assert C.heatbath_step == 3
+        p, l = C.run(2, 1, 2)
+        assert np.array_equal(C.export_links(), ref)
+        assert np.array_equal(p, ref_p[3:]) and np.array_equal(l, ref_l[3:])
+
+
+def test_mismatched_lattice_is_refused_and_unchanged(sunlib, tmp_path):
+    path = tmp_path / "a.cfg"
+    with sunlib.Lattice(3, (4, 4, 4, 4), 6.0, hot_start=True, seed=3) as A:
+        A.save(path)
+    for kw in (dict(dims=(4, 4, 4, 6)), dict(storage=18), dict(precision=64), dict(nc=2, storage=4)):
+        args = dict(nc=3, dims=(4, 4, 4, 4), storage=12, precision=32)
+        args.update(kw)
+        with sunlib.Lattice(args["nc"], args["dims"], 6.0, hot_start=True, seed=4, storage=args["storage"],
+                            precision=args["precision"]) as B:
+            before = B.export_links()
+            with pytest.raises(sunlib.SunError):
+                B.load(path)
+            assert np.array_equal(B.export_links(), before)
+
+
+def test_damaged_file_leaves_the_lattice_unchanged(sunlib, tmp_path):
+    path = tmp_path / "b.cfg"
+    with sunlib.Lattice(3, (4, 4, 4, 4), 6.0, hot_start=True, seed=5) as A:
+        A.save(path)
+    data = bytearray(open(path, "rb").read())
+    data[200] ^= 0x40  # one bit of the payload
+    open(path, "wb").write(bytes(data))
+    with sunlib.Lattice(3, (4, 4, 4, 4), 6.0, hot_start=True, seed=6) as B:
+        before = B.export_links()
+        step = B.heatbath_step
+        with pytest.raises(sunlib.SunError):
+            B.load(path)
+        assert np.array_equal(B.export_links(), before) and B.heatbath_step == step
