@@ -91,7 +91,10 @@ enum { SUN_HEATBATH = 0, SUN_OVERRELAX = 1 };
  *                the two parities share are re-read from L2, not HBM).  Kernels
  *                without this form (row-parallel, bit 2) run the two passes.
  *                The device-side waits are bounded: one that gives up after
- *                2 s makes sun_run / sun_synchronize return SUN_ERR_TIMEOUT.
+ *                2 s makes sun_run / sun_synchronize return SUN_ERR_TIMEOUT;
+ *                16 = (SU(3) FP32) overrelaxation passes compute two links per
+ *                thread with packed FP32 instructions ({add,sub,mul,fma}.f32x2),
+ *                lane for lane the float operations: bitwise the same links.
  *  reunit_mode   where a sweep re-unitarizes (default 0); every link is
  *                re-unitarized once per re-unitarizing sweep in all three:
  *                0 = all links after the sweep's last step, as a pass of its own

@@ -323,7 +323,7 @@ static sun_status resolve(int nc, const int* dims, const sun_options* opt_in, su
   if (opt->storage == 0) opt->storage = default_storage(nc);
   if (opt->reunit_every < 0) return fail(SUN_ERR_ARG, "reunit_every must be >= 0");
   if (opt->block_threads == 0) opt->block_threads = 128;
-  if (opt->variant < 0 || opt->variant > 15) return fail(SUN_ERR_ARG, "variant = %d must be in 0..15", opt->variant);
+  if (opt->variant < 0 || opt->variant > 31) return fail(SUN_ERR_ARG, "variant = %d must be in 0..31", opt->variant);
   if (opt->wave_lag < 0) return fail(SUN_ERR_ARG, "wave_lag = %d must be >= 0", opt->wave_lag);
   if (opt->wave_lag == 0) opt->wave_lag = kDefaultWaveLag;
   if (opt->wave_skip_units < 0) return fail(SUN_ERR_ARG, "wave_skip_units must be >= 0");

@@ -77,6 +77,55 @@ __device__ __forceinline__ void ccfma(Cpx<R>& acc, Cpx<R> a, Cpx<R> b) {
   acc.im = fma(-a.im, b.re, acc.im);
 }
 
+// ----------------------------------------------------- packed FP32 pairs ----
+// Two FP32 values handled by one packed instruction ({add,sub,mul,fma}.rn.f32x2,
+// sm_100 and later): each lane is the same IEEE round-to-nearest operation as
+// the float one, so code written for a real type R and run with R = F2 computes
+// two independent problems (two links) with the results of the float code for
+// each, in half the arithmetic instructions.
+struct F2 {
+  unsigned long long v;
+  F2() = default;
+  __device__ __forceinline__ explicit F2(float s) { asm("mov.b64 %0, {%1, %1};" : "=l"(v) : "f"(s)); }
+};
+
+using ::fma;  // the float and double overloads stay visible beside the F2 one
+
+__device__ __forceinline__ F2 f2_pack(float lo, float hi) {
+  F2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(F2 a, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a.v));
+}
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) {
+  F2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) {
+  F2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) {
+  F2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+// negation flips the two sign bits (exact, as float negation)
+__device__ __forceinline__ F2 operator-(F2 a) {
+  F2 r;
+  r.v = a.v ^ 0x8000000080000000ull;
+  return r;
+}
+__device__ __forceinline__ F2 fma(F2 a, F2 b, F2 c) {
+  F2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+  return r;
+}
+
 // -------------------------------------------------------------- matrices ----
 template <class R, int N>
 struct Mat {

@@ -955,6 +955,156 @@ __global__ void __launch_bounds__(kMaxBlockThreads) update_pair_quat(const PassP
   wavefront<R, 2, kQuat, MODE, false, REUNIT, true>(p, w);
 }
 
+// ---------------------------------------------------------------------------
+// Overrelaxation pass with two links per thread in packed FP32 (variant bit 16,
+// SU(3) FP32 storage).  Lane 0 of every F2 value belongs to half-site h0, lane 1
+// to h1 = h0 + blockDim.x; the staple, W = U Sigma^+ and the subgroup updates
+// are the float templates run with R = F2, so every link gets bitwise the
+// result of the one-link kernel in half the FP32 instructions (the pass is
+// bound by instruction issue).  Square roots and divisions are per lane.
+// ---------------------------------------------------------------------------
+template <int N, int S, int KL>
+__device__ __forceinline__ Mat<F2, N> load_mat2(const char* blk, int64_t Vh, int64_t h0, int64_t h1) {
+  constexpr int NR = Layout<float, N, S>::nreals;
+  float r0[NR], r1[NR];
+  load_reals<float, NR, KL>(blk, Vh, h0, r0);
+  load_reals<float, NR, KL>(blk, Vh, h1, r1);
+  Mat<F2, N> m;
+  constexpr int rows = S == kTwoRow ? 2 : N;
+#pragma unroll
+  for (int i = 0; i < rows; ++i)
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+      m.e[i][j] = {f2_pack(r0[2 * (N * i + j)], r1[2 * (N * i + j)]),
+                   f2_pack(r0[2 * (N * i + j) + 1], r1[2 * (N * i + j) + 1])};
+  if constexpr (S == kTwoRow) su3_third_row(m);
+  return m;
+}
+
+template <int N, int S>
+__device__ __forceinline__ void store_mat2(char* blk, int64_t Vh, int64_t h0, int64_t h1, bool store1,
+                                           const Mat<F2, N>& m) {
+  Mat<float, N> a, b;
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      f2_unpack(m.e[i][j].re, a.e[i][j].re, b.e[i][j].re);
+      f2_unpack(m.e[i][j].im, a.e[i][j].im, b.e[i][j].im);
+    }
+  store_mat<float, N, S>(blk, Vh, h0, a);
+  if (store1) store_mat<float, N, S>(blk, Vh, h1, b);
+}
+
+template <int N>
+__device__ __forceinline__ Mat<double, N> lane_to_double(const Mat<F2, N>& m, int lane) {
+  Mat<double, N> d;
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      float r0, r1, i0, i1;
+      f2_unpack(m.e[i][j].re, r0, r1);
+      f2_unpack(m.e[i][j].im, i0, i1);
+      d.e[i][j] = {double(lane ? r1 : r0), double(lane ? i1 : i0)};
+    }
+  return d;
+}
+
+template <int N, int S, bool REUNIT>
+__device__ __forceinline__ void or_pass_body2(const PassParams& p, int par, int64_t h0, int64_t h1, bool act1) {
+  const Geom& g = p.g;
+  const int mu = p.mu, opp = par ^ 1;
+  const Site s0 = decode_half(g, h0, par), s1 = decode_half(g, h1, par);
+  const uint32_t lex0 = uint32_t(s0.lex), lex1 = uint32_t(s1.lex);
+  const int cmu0 = coord_of(s0, mu), cmu1 = coord_of(s1, mu);
+  const uint32_t pmu0 = fwd(g, lex0, cmu0, mu), pmu1 = fwd(g, lex1, cmu1, mu);
+
+  Mat<F2, N> st;
+  mat_zero(st);
+#pragma unroll
+  for (int nu = 0; nu < 4; ++nu) {
+    if (nu == mu) continue;
+    const uint32_t pnu0 = fwd(g, lex0, s0.c[nu], nu), pnu1 = fwd(g, lex1, s1.c[nu], nu);
+    const uint32_t mnu0 = bwd(g, lex0, s0.c[nu], nu), mnu1 = bwd(g, lex1, s1.c[nu], nu);
+    const uint32_t mnpm0 = fwd(g, mnu0, cmu0, mu), mnpm1 = fwd(g, mnu1, cmu1, mu);
+    {  // U_nu(x) U_mu(x+nu) U_nu(x+mu)^+
+      const Mat<F2, N> a = load_mat2<N, S, kLoadNc>(block_ptr(p, nu, par), g.Vh, h0, h1);
+      const Mat<F2, N> b = load_mat2<N, S, kLoadNc>(block_ptr(p, mu, opp), g.Vh, pnu0 >> 1, pnu1 >> 1);
+      const Mat<F2, N> t = mul_nn(a, b);
+      const Mat<F2, N> c = load_mat2<N, S, kLoadNc>(block_ptr(p, nu, opp), g.Vh, pmu0 >> 1, pmu1 >> 1);
+      acc_nd(st, t, c);
+    }
+    {  // U_nu(x-nu)^+ U_mu(x-nu) U_nu(x-nu+mu)
+      const Mat<F2, N> a = load_mat2<N, S, kLoadNc>(block_ptr(p, nu, opp), g.Vh, mnu0 >> 1, mnu1 >> 1);
+      const Mat<F2, N> b = load_mat2<N, S, kLoadNc>(block_ptr(p, mu, opp), g.Vh, mnu0 >> 1, mnu1 >> 1);
+      const Mat<F2, N> t = mul_dn(a, b);
+      const Mat<F2, N> c = load_mat2<N, S, kLoadNc>(block_ptr(p, nu, par), g.Vh, mnpm0 >> 1, mnpm1 >> 1);
+      acc_nn(st, t, c);
+    }
+  }
+
+  char* ublk = p.links + (2 * mu + par) * p.block_bytes;
+  Mat<F2, N> u = load_mat2<N, S, kLoadPlain>(ublk, g.Vh, h0, h1);
+  Mat<F2, N> w = mul_nd(u, st);
+
+#pragma unroll
+  for (int i = 0; i < N - 1; ++i) {
+#pragma unroll
+    for (int j = i + 1; j < N; ++j) {
+      const bool last = (i == N - 2) && (j == N - 1);
+      const Quat<F2> v = block_to_quat(w.e[i][i], w.e[i][j], w.e[j][i], w.e[j][j]);
+      float k0, k1;
+      f2_unpack(fma(v.a0, v.a0, fma(v.a1, v.a1, fma(v.a2, v.a2, v.a3 * v.a3))), k0, k1);
+      k0 = sqrtf(k0);
+      k1 = sqrtf(k1);
+      const bool ok0 = k0 > 1e-15f && isfinite(k0), ok1 = k1 > 1e-15f && isfinite(k1);
+      const F2 inv = f2_pack(ok0 ? 1.0f / k0 : 0.0f, ok1 ? 1.0f / k1 : 0.0f);
+      const Quat<F2> vd = {v.a0 * inv, -v.a1 * inv, -v.a2 * inv, -v.a3 * inv};  // vhat^+
+      Quat<F2> a = qmul(vd, vd);
+      if (!(ok0 && ok1)) {
+        // a skipped subgroup of one lane: the identity there (applies exactly)
+        float x0, x1;
+        f2_unpack(a.a0, x0, x1);
+        a.a0 = f2_pack(ok0 ? x0 : 1.0f, ok1 ? x1 : 1.0f);
+        f2_unpack(a.a1, x0, x1);
+        a.a1 = f2_pack(ok0 ? x0 : 0.0f, ok1 ? x1 : 0.0f);
+        f2_unpack(a.a2, x0, x1);
+        a.a2 = f2_pack(ok0 ? x0 : 0.0f, ok1 ? x1 : 0.0f);
+        f2_unpack(a.a3, x0, x1);
+        a.a3 = f2_pack(ok0 ? x0 : 0.0f, ok1 ? x1 : 0.0f);
+      }
+      apply_rows(u, i, j, a);
+      if (!last) apply_rows(w, i, j, a);
+    }
+  }
+  if constexpr (REUNIT) {
+    Mat<float, N> f[2];
+#pragma unroll
+    for (int lane = 0; lane < 2; ++lane) {
+      Mat<double, N> d = lane_to_double<N>(u, lane);
+      if (reunit_selected(p, lane ? h1 : h0)) reunit_d<N>(d);
+      f[lane] = mat_cast<double, float, N>(d);
+    }
+#pragma unroll
+    for (int a = 0; a < N; ++a)
+#pragma unroll
+      for (int b = 0; b < N; ++b)
+        u.e[a][b] = {f2_pack(f[0].e[a][b].re, f[1].e[a][b].re), f2_pack(f[0].e[a][b].im, f[1].e[a][b].im)};
+  }
+  store_mat2<N, S>(ublk, g.Vh, h0, h1, act1, u);
+}
+
+template <int N, int S, bool REUNIT>
+__global__ void __launch_bounds__(128) update_or_pass2(const PassParams p) {
+  const int64_t h0 = int64_t(blockIdx.x) * (2 * blockDim.x) + threadIdx.x;
+  if (h0 >= p.g.Vh) return;
+  int64_t h1 = h0 + blockDim.x;
+  const bool act1 = h1 < p.g.Vh;
+  if (!act1) h1 = h0;  // the ragged tail: lane 1 repeats lane 0 and is not stored
+  or_pass_body2<N, S, REUNIT>(p, p.parity, h0, h1, act1);
+}
+
 struct LinkParams {
   char* links;
   int64_t block_bytes;
@@ -1526,6 +1676,15 @@ cudaError_t launch_pass(const Ctx& c, int mode, int mu, int parity, uint32_t ste
     }
 #undef SUN_LAUNCH_QUAT
   } else if constexpr (has_variants<R, N, S>()) {
+    if ((c.variant & 16) && mode == kOverrelaxMode) {
+      // two links per thread in packed FP32
+      const unsigned g2 = unsigned((c.g.Vh + 255) / 256);
+      if (ru)
+        update_or_pass2<N, S, true><<<g2, 128, 0, c.stream>>>(p);
+      else
+        update_or_pass2<N, S, false><<<g2, 128, 0, c.stream>>>(p);
+      return cudaGetLastError();
+    }
     const int v = c.variant & 3;
     const unsigned bt1 = (v & 1) ? 128u : unsigned(bt);
     const unsigned g1 = unsigned((c.g.Vh + bt1 - 1) / bt1);
@@ -1599,14 +1758,14 @@ cudaError_t launch_pair_mat(const Ctx& c, int mode, bool ru, int bt, const PassP
 }
 
 // The even and the odd pass of direction mu.  Kernels without a wavefront form
-// (the row-parallel kernel, the two-row staple variant) run as the two passes.
+// (the row-parallel kernel, the two-row staple and packed variants) run as the two passes.
 template <class R, int N, int S>
 cudaError_t launch_pair(const Ctx& c, int mode, int mu, uint32_t step_offset, uint32_t reunit_mod,
                         uint32_t reunit_rem) {
   const bool ru = reunit_mod != 0u;
   bool two = !c.wave;
   if constexpr (has_group<R, N>()) two = two || (!ru && use_group<R, N>(c.variant));
-  if constexpr (has_variants<R, N, S>()) two = two || (c.variant & 2) != 0;
+  if constexpr (has_variants<R, N, S>()) two = two || (c.variant & 18) != 0;
   if (two) {
     const cudaError_t e = launch_pass<R, N, S>(c, mode, mu, 0, step_offset, reunit_mod, reunit_rem);
     if (e != cudaSuccess) return e;

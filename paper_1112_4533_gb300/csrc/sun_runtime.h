@@ -63,7 +63,8 @@ struct Ctx {
   int reduce_blocks;
   int obs_stride, obs_offset;  // observable output: row stride and column (1, 0 for one lattice)
   int variant;  // update-pass kernel variant (1: 5 blocks/SM register bound, 2: two-row staple, 4: swap row-parallel / per-link
-                // kernel for Nc 4, 6, 8: even and odd pass of a direction in one wavefront launch)
+                // kernel for Nc 4, 6, 8: even and odd pass of a direction in one wavefront launch,
+                // 16: two links per thread in packed FP32 for SU(3) FP32 overrelaxation)
   uint32_t* wave;  // kWaveSyncWords + Nt words of wavefront synchronisation
   int wave_lag;    // t-slices the even units of a wavefront run ahead of the odd ones
   uint32_t wave_skip;  // fault injection: leading units every wavefront launch leaves out (0 normally)
