@@ -282,6 +282,32 @@ sun_status sun_batch_run(sun_batch* b, int n_sweeps, int n_heatbath, int n_overr
 void sun_batch_destroy(sun_batch* b); /* syncs; the lattices are not touched */
 
 /* ---------------------------------------------------------------------------
+ * t-slab decomposition (Sec. 3: the paper splits the lattice in the time
+ * direction over GPUs and exchanges the border slices).  The lattice is cut
+ * into n_slabs slabs of Nt / n_slabs consecutive t-slices (an even number);
+ * each slab is a lattice of its own with one halo slice on each side.  After
+ * every chessboard pass (direction mu, parity) each slab copies the two
+ * boundary slices of that (mu, parity) block into its neighbours' halos, so the
+ * next pass reads exactly the links the whole lattice would hold.  Random
+ * numbers are keyed by each link's index in the whole lattice, so the slabs
+ * produce bitwise the links of one lattice with the same seed; the plaquette
+ * and Polyakov loop agree to FP64 summation order.  All slabs live on the
+ * current device and share one stream (a stand-in for one GPU per slab: the
+ * halo copies are device-to-device transfers of contiguous slices).  Options
+ * as for a lattice, except device_buf (must be NULL) and reunit_every (0 or 1).
+ */
+typedef struct sun_slabs sun_slabs;
+sun_status sun_slabs_create(sun_slabs** out, int nc, const int dims[4], int n_slabs, double beta,
+                            int hot_start, uint64_t seed, const sun_options* opt);
+void sun_slabs_destroy(sun_slabs* slabs); /* syncs; NULL is a no-op */
+/* n_sweeps sweeps as sun_run, with the histories of the whole lattice.  Syncs. */
+sun_status sun_slabs_run(sun_slabs* slabs, int n_sweeps, int n_heatbath, int n_overrelax,
+                         double* plaq_hist, double* poly_hist);
+/* the whole lattice in canonical order, as sun_export_links / sun_import_links (pageable host memory). */
+sun_status sun_slabs_export_links(sun_slabs* slabs, double* host, size_t n_doubles);
+sun_status sun_slabs_import_links(sun_slabs* slabs, const double* host, size_t n_doubles);
+
+/* ---------------------------------------------------------------------------
  * Autotuning.  The paper tunes its kernels by hand for its GPU (Sec. 3: threads
  * per block, storage format, read path); here the configuration is measured on
  * the GPU at hand.  Scratch lattices of the requested shape (hot start) are

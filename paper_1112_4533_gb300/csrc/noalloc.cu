@@ -117,6 +117,10 @@ extern "C" sun_status sun_plaquette_noalloc(const void* links, int nc, const int
   c.stream = static_cast<cudaStream_t>(stream);
   c.block_threads = 128;
   c.reduce_blocks = kNoAllocMaxBlocks;  // one block per 256 sites: ceil(V/256) <= 65536
+  c.h_begin = 0;  // the whole lattice
+  c.h_end = g.Vh;
+  c.lex_offset = 0u;
+  c.v_global = uint32_t(V);
 
   // the array keeps the last call's contents: re-arm the completion counter
   if (cudaMemsetAsync(c.state, 0, sizeof(sun::DevState), c.stream) != cudaSuccess) {

@@ -44,12 +44,26 @@ struct PassParams {
   const uint32_t* hb_step;
   uint32_t step_offset;
   // FP64 re-unitarization right after the update of the links whose run of 32
-  // half-site indices r = h >> 5 has r % reunit_mod == reunit_rem (0 = none)
+  // half-site indices r = h >> 5 (of the whole lattice) has r % reunit_mod ==
+  // reunit_rem (0 = none)
   uint32_t reunit_mod, reunit_rem;
+  // The pass covers half-sites [h_begin, h_end) of this (local) lattice.  A slab
+  // of a lattice cut into t-slabs is a local lattice with one halo slice on each
+  // side: its site lex is site (lex + lex_offset) mod v_global of the whole
+  // lattice, which keys the random numbers and the re-unitarization runs.
+  int64_t h_begin, h_end;
+  uint32_t lex_offset, v_global;
 };
 
-__device__ __forceinline__ bool reunit_selected(const PassParams& p, int64_t h) {
-  return p.reunit_mod != 0u && ((uint32_t(h) >> 5) % p.reunit_mod) == p.reunit_rem;
+// index of a local site in the whole lattice
+__device__ __forceinline__ uint32_t global_lex(const PassParams& p, uint32_t lex) {
+  const uint32_t l = lex + p.lex_offset;
+  return l >= p.v_global ? l - p.v_global : l;
+}
+
+// hg: the half-site index in the whole lattice
+__device__ __forceinline__ bool reunit_selected(const PassParams& p, int64_t hg) {
+  return p.reunit_mod != 0u && ((uint32_t(hg) >> 5) % p.reunit_mod) == p.reunit_rem;
 }
 
 __device__ __forceinline__ const char* block_ptr(const PassParams& p, int d, int par) {
@@ -360,7 +374,8 @@ __device__ __forceinline__ void pass_body(const PassParams& p, int par, int64_t 
 
   uint32_t step = 0;
   if constexpr (MODE == kHeatbathMode) step = *p.hb_step + p.step_offset;
-  const uint32_t link_id = uint32_t(mu) * uint32_t(g.V) + lex;
+  const uint32_t glex = global_lex(p, lex);
+  const uint32_t link_id = uint32_t(mu) * p.v_global + glex;
   const R alpha_coef = R(p.alpha_coef);
 
   int sub = 0;
@@ -392,7 +407,7 @@ __device__ __forceinline__ void pass_body(const PassParams& p, int par, int64_t 
     }
   }
   if constexpr (REUNIT) {
-    if (reunit_selected(p, h)) {
+    if (reunit_selected(p, glex >> 1)) {
       Mat<double, N> d = mat_cast<R, double, N>(u);
       reunit_d<N>(d);
       u = mat_cast<double, R, N>(d);
@@ -407,15 +422,15 @@ __device__ __forceinline__ void pass_body(const PassParams& p, int par, int64_t 
 // re-unitarize use this instantiation; the others carry no FP64 code).
 template <class R, int N, int S, int MODE, int VAR, bool REUNIT>
 __global__ void __launch_bounds__(kMaxBlockThreads) update_pass_mat(const PassParams p) {
-  const int64_t h = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (h >= p.g.Vh) return;
+  const int64_t h = p.h_begin + int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (h >= p.h_end) return;
   pass_body<R, N, S, MODE, (VAR & 2) != 0, REUNIT>(p, p.parity, h);
 }
 
 template <class R, int N, int S, int MODE, int VAR, bool REUNIT>
 __global__ void __launch_bounds__(128, kOccBlocks) update_pass_mat_occ(const PassParams p) {
-  const int64_t h = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (h >= p.g.Vh) return;
+  const int64_t h = p.h_begin + int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (h >= p.h_end) return;
   pass_body<R, N, S, MODE, (VAR & 2) != 0, REUNIT>(p, p.parity, h);
 }
 
@@ -663,7 +678,8 @@ __device__ __forceinline__ void group_pass_body(const PassParams& p, int64_t h, 
 
   uint32_t step = 0;
   if constexpr (MODE == kHeatbathMode) step = *p.hb_step + p.step_offset;
-  const uint32_t link_id = uint32_t(mu) * uint32_t(g.V) + lex;
+  const uint32_t glex = global_lex(p, lex);
+  const uint32_t link_id = uint32_t(mu) * p.v_global + glex;
   const R alpha_coef = R(p.alpha_coef);
   int sub = 0;
 #pragma unroll
@@ -742,7 +758,7 @@ __global__ void __launch_bounds__(128) update_pass_group(const PassParams p) {
   int64_t h;
   bool active;
   int r, base, slot;
-  group_lane<R, N>(int64_t(blockIdx.x) * Group<R, N>::LPB, p.g.Vh, h, active, r, base, slot);
+  group_lane<R, N>(p.h_begin + int64_t(blockIdx.x) * Group<R, N>::LPB, p.h_end, h, active, r, base, slot);
   group_pass_body<R, N, MODE>(p, h, active, r, base, sm[slot]);
 }
 
@@ -803,7 +819,7 @@ __device__ __forceinline__ void quat_pass_body(const PassParams& p, int par, int
     const Quat<R> vd = {w.a0 * inv, -w.a1 * inv, -w.a2 * inv, -w.a3 * inv};
     if constexpr (MODE == kHeatbathMode) {
       const uint32_t step = *p.hb_step + p.step_offset;
-      const uint32_t link_id = uint32_t(mu) * uint32_t(g.V) + uint32_t(s.lex);
+      const uint32_t link_id = uint32_t(mu) * p.v_global + global_lex(p, lex);
       Quat<R> b;
       if (heatbath_su2<R>(R(p.alpha_coef) * k, p.key, link_id, step, 0u, b)) u = qmul(qmul(b, vd), u);
     } else {
@@ -811,7 +827,7 @@ __device__ __forceinline__ void quat_pass_body(const PassParams& p, int par, int
     }
   }
   if constexpr (REUNIT) {
-    if (reunit_selected(p, h)) {
+    if (reunit_selected(p, global_lex(p, lex) >> 1)) {
       const double a0 = u.a0, a1 = u.a1, a2 = u.a2, a3 = u.a3;
       const double inv = rsqrt_near_one(fma(a1, a1, fma(a2, a2, fma(a3, a3, a0 * a0))));
       u = Quat<R>{R(a0 * inv), R(a1 * inv), R(a2 * inv), R(a3 * inv)};
@@ -822,8 +838,8 @@ __device__ __forceinline__ void quat_pass_body(const PassParams& p, int par, int
 
 template <class R, int MODE, bool REUNIT>
 __global__ void __launch_bounds__(kMaxBlockThreads) update_pass_quat(const PassParams p) {
-  const int64_t h = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (h >= p.g.Vh) return;
+  const int64_t h = p.h_begin + int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (h >= p.h_end) return;
   quat_pass_body<R, MODE, REUNIT>(p, p.parity, h);
 }
 
@@ -1083,7 +1099,7 @@ __device__ __forceinline__ void or_pass_body2(const PassParams& p, int par, int6
 #pragma unroll
     for (int lane = 0; lane < 2; ++lane) {
       Mat<double, N> d = lane_to_double<N>(u, lane);
-      if (reunit_selected(p, lane ? h1 : h0)) reunit_d<N>(d);
+      if (reunit_selected(p, global_lex(p, lane ? lex1 : lex0) >> 1)) reunit_d<N>(d);
       f[lane] = mat_cast<double, float, N>(d);
     }
 #pragma unroll
@@ -1097,10 +1113,10 @@ __device__ __forceinline__ void or_pass_body2(const PassParams& p, int par, int6
 
 template <int N, int S, bool REUNIT>
 __global__ void __launch_bounds__(128) update_or_pass2(const PassParams p) {
-  const int64_t h0 = int64_t(blockIdx.x) * (2 * blockDim.x) + threadIdx.x;
-  if (h0 >= p.g.Vh) return;
+  const int64_t h0 = p.h_begin + int64_t(blockIdx.x) * (2 * blockDim.x) + threadIdx.x;
+  if (h0 >= p.h_end) return;
   int64_t h1 = h0 + blockDim.x;
-  const bool act1 = h1 < p.g.Vh;
+  const bool act1 = h1 < p.h_end;
   if (!act1) h1 = h0;  // the ragged tail: lane 1 repeats lane 0 and is not stored
   or_pass_body2<N, S, REUNIT>(p, p.parity, h0, h1, act1);
 }
@@ -1111,6 +1127,7 @@ struct LinkParams {
   Geom g;
   uint2 key;
   int hot;
+  uint32_t lex_offset, v_global;  // a slab's place in the whole lattice (as in PassParams)
 };
 
 template <class R, int N, int S>
@@ -1148,7 +1165,9 @@ __global__ void __launch_bounds__(256) init_kernel(const LinkParams p) {
     mat_identity(m);
   } else {
     const Site s = decode_half(p.g, h, par);
-    const uint32_t link_id = uint32_t(mu) * uint32_t(p.g.V) + uint32_t(s.lex);
+    uint32_t glex = uint32_t(s.lex) + p.lex_offset;
+    if (glex >= p.v_global) glex -= p.v_global;
+    const uint32_t link_id = uint32_t(mu) * p.v_global + glex;
     constexpr int kNormals = 2 * N * N;
     double gauss[kNormals + 3];
 #pragma unroll
@@ -1234,6 +1253,7 @@ struct ObsParams {
   const char* links;
   int64_t block_bytes;
   Geom g;
+  int64_t h_begin, h_end;  // half-sites measured (per parity); a slab's interior slices
 };
 
 __device__ __forceinline__ const char* obs_block(const ObsParams& p, int d, int par) {
@@ -1241,13 +1261,11 @@ __device__ __forceinline__ const char* obs_block(const ObsParams& p, int d, int 
 }
 
 // Sum over the six plaquettes P_{mu nu}(x) = U_mu(x) U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+
-// (Eq. 4) of one site (idx < V in parity-block order), ReTr in the storage
+// (Eq. 4) of one site (half-site h of parity par), ReTr in the storage
 // precision, each added in FP64.
 template <class R, int N, int S>
-__device__ __forceinline__ double site_plaquette(const ObsParams& p, int64_t idx) {
+__device__ __forceinline__ double site_plaquette(const ObsParams& p, int par, int64_t h) {
   const Geom& g = p.g;
-  const int par = idx >= g.Vh ? 1 : 0;
-  const int64_t h = idx - par * g.Vh;
   const Site s = decode_half(g, h, par);
   const uint32_t lex = uint32_t(s.lex);
   double acc = 0.0;
@@ -1316,9 +1334,12 @@ __device__ __forceinline__ void site_polyakov(const ObsParams& p, int64_t xs, do
 template <class R, int N, int S>
 __global__ void __launch_bounds__(256) plaquette_kernel(const ObsParams p, const ReduceParams rp) {
   double acc[1] = {0.0};
-  for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < p.g.V;
-       idx += int64_t(gridDim.x) * blockDim.x)
-    acc[0] += site_plaquette<R, N, S>(p, idx);
+  const int64_t cnt = p.h_end - p.h_begin;  // sites per parity (all of them: Vh)
+  for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < 2 * cnt;
+       idx += int64_t(gridDim.x) * blockDim.x) {
+    const int par = idx >= cnt ? 1 : 0;
+    acc[0] += site_plaquette<R, N, S>(p, par, p.h_begin + idx - par * cnt);
+  }
   reduce_finish<1>(acc, rp);
 }
 
@@ -1333,6 +1354,65 @@ __global__ void __launch_bounds__(256) polyakov_kernel(const ObsParams p, const 
     site_polyakov<R, N, S>(p, xs, re, im);
     acc[0] += re;
     acc[1] += im;
+  }
+  reduce_finish<2>(acc, rp);
+}
+
+// ---------------------------------------------------------------------------
+// Polyakov loop of a lattice cut into t-slabs: each slab multiplies U_t over its
+// interior slices, in t order, at every spatial site; then the slabs' partial
+// products are multiplied in slab order and traced (storage precision products,
+// FP64 trace and sum, as for one lattice).
+// ---------------------------------------------------------------------------
+template <class R, int N, int S>
+using PolyPart = typename std::conditional<S == kQuat, Quat<R>, Mat<R, N>>::type;
+
+template <class R, int N, int S>
+__global__ void __launch_bounds__(128) polyakov_partial_kernel(const ObsParams p, int t_begin, int t_end, void* out) {
+  const Geom& g = p.g;
+  const int64_t nsp = int64_t(g.nx) * g.ny * g.nz;
+  const int64_t xs = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (xs >= nsp) return;
+  const int x = int(xs % g.nx);
+  const int y = int((xs / g.nx) % g.ny);
+  const int z = int(xs / (int64_t(g.nx) * g.ny));
+  const int sp = (x + y + z) & 1;
+  PolyPart<R, N, S>* o = static_cast<PolyPart<R, N, S>*>(out);
+  if constexpr (S == kQuat) {
+    Quat<R> P = load_quat<R>(obs_block(p, 3, (sp + t_begin) & 1), g.Vh, (xs + int64_t(t_begin) * nsp) >> 1);
+    for (int t = t_begin + 1; t < t_end; ++t)
+      P = qmul(P, load_quat<R>(obs_block(p, 3, (sp + t) & 1), g.Vh, (xs + int64_t(t) * nsp) >> 1));
+    o[xs] = P;
+  } else {
+    Mat<R, N> P = load_mat<R, N, S>(obs_block(p, 3, (sp + t_begin) & 1), g.Vh, (xs + int64_t(t_begin) * nsp) >> 1);
+    for (int t = t_begin + 1; t < t_end; ++t)
+      P = mul_nn(P, load_mat<R, N, S>(obs_block(p, 3, (sp + t) & 1), g.Vh, (xs + int64_t(t) * nsp) >> 1));
+    o[xs] = P;
+  }
+}
+
+template <class R, int N, int S>
+__global__ void __launch_bounds__(128) polyakov_combine_kernel(const void* const* parts, int n, int64_t nsp,
+                                                               const ReduceParams rp) {
+  double acc[2] = {0.0, 0.0};
+  for (int64_t xs = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; xs < nsp; xs += int64_t(gridDim.x) * blockDim.x) {
+    PolyPart<R, N, S> P = static_cast<const PolyPart<R, N, S>*>(parts[0])[xs];
+    for (int k = 1; k < n; ++k) {
+      const PolyPart<R, N, S> Q = static_cast<const PolyPart<R, N, S>*>(parts[k])[xs];
+      if constexpr (S == kQuat)
+        P = qmul(P, Q);
+      else
+        P = mul_nn(P, Q);
+    }
+    if constexpr (S == kQuat) {
+      acc[0] += double(R(2) * P.a0);
+    } else {
+#pragma unroll
+      for (int d = 0; d < N; ++d) {
+        acc[0] += double(P.e[d][d].re);
+        acc[1] += double(P.e[d][d].im);
+      }
+    }
   }
   reduce_finish<2>(acc, rp);
 }
@@ -1375,6 +1455,10 @@ __device__ __forceinline__ void batch_pass_body(const BatchParams& bp, int mu, i
     sp.step_offset = step_offset;
     sp.reunit_mod = rmod;
     sp.reunit_rem = rrem;
+    sp.h_begin = 0;
+    sp.h_end = d.g.Vh;
+    sp.lex_offset = 0u;
+    sp.v_global = uint32_t(d.g.V);
   }
   __syncthreads();
   const PassParams p = sp;  // a private copy: the body need not re-read shared memory
@@ -1420,6 +1504,10 @@ __global__ void __launch_bounds__(128)
     sp.step_offset = step_offset;
     sp.reunit_mod = 0u;
     sp.reunit_rem = 0u;
+    sp.h_begin = 0;
+    sp.h_end = d.g.Vh;
+    sp.lex_offset = 0u;
+    sp.v_global = uint32_t(d.g.V);
   }
   __syncthreads();
   const PassParams p = sp;  // a private copy: the body's __syncwarp()s would force re-reads of shared memory
@@ -1439,6 +1527,8 @@ __device__ __forceinline__ void batch_obs_chain(const BatchParams& bp, ObsParams
     sp.links = d.links;
     sp.block_bytes = d.block_bytes;
     sp.g = d.g;
+    sp.h_begin = 0;
+    sp.h_end = d.g.Vh;
   }
   __syncthreads();
 }
@@ -1494,7 +1584,8 @@ __global__ void __launch_bounds__(256) plaquette_batch(const BatchParams bp, dou
   __shared__ uint32_t first;
   batch_obs_chain(bp, sp, first);
   const int64_t idx = int64_t(blockIdx.x - first) * blockDim.x + threadIdx.x;
-  double v[1] = {idx < sp.g.V ? site_plaquette<R, N, S>(sp, idx) : 0.0};
+  const int par = idx >= sp.g.Vh ? 1 : 0;
+  double v[1] = {idx < sp.g.V ? site_plaquette<R, N, S>(sp, par, idx - par * sp.g.Vh) : 0.0};
   block_sum<1>(v);
   if (threadIdx.x == 0) partials[blockIdx.x] = v[0];
 }
@@ -1637,6 +1728,10 @@ inline PassParams make_pass_params(const Ctx& c, int mu, int parity, uint32_t st
   p.step_offset = step_offset;
   p.reunit_mod = reunit_mod;
   p.reunit_rem = reunit_rem;
+  p.h_begin = c.h_begin;
+  p.h_end = c.h_end;
+  p.lex_offset = c.lex_offset;
+  p.v_global = c.v_global;
   return p;
 }
 
@@ -1645,11 +1740,12 @@ cudaError_t launch_pass(const Ctx& c, int mode, int mu, int parity, uint32_t ste
                         uint32_t reunit_rem) {
   const PassParams p = make_pass_params(c, mu, parity, step_offset, reunit_mod, reunit_rem);
   const int bt = c.block_threads;
-  const unsigned grid = unsigned((c.g.Vh + bt - 1) / bt);
+  const int64_t n_links = c.h_end - c.h_begin;
+  const unsigned grid = unsigned((n_links + bt - 1) / bt);
   const bool ru = reunit_mod != 0u;
   if constexpr (has_group<R, N>()) {
     if (!ru && use_group<R, N>(c.variant)) {
-      const unsigned gg = unsigned((c.g.Vh + Group<R, N>::LPB - 1) / Group<R, N>::LPB);
+      const unsigned gg = unsigned((n_links + Group<R, N>::LPB - 1) / Group<R, N>::LPB);
       if (mode == kHeatbathMode)
         update_pass_group<R, N, kHeatbathMode><<<gg, 128, 0, c.stream>>>(p);
       else
@@ -1678,7 +1774,7 @@ cudaError_t launch_pass(const Ctx& c, int mode, int mu, int parity, uint32_t ste
   } else if constexpr (has_variants<R, N, S>()) {
     if ((c.variant & 16) && mode == kOverrelaxMode) {
       // two links per thread in packed FP32
-      const unsigned g2 = unsigned((c.g.Vh + 255) / 256);
+      const unsigned g2 = unsigned((n_links + 255) / 256);
       if (ru)
         update_or_pass2<N, S, true><<<g2, 128, 0, c.stream>>>(p);
       else
@@ -1687,7 +1783,7 @@ cudaError_t launch_pass(const Ctx& c, int mode, int mu, int parity, uint32_t ste
     }
     const int v = c.variant & 3;
     const unsigned bt1 = (v & 1) ? 128u : unsigned(bt);
-    const unsigned g1 = unsigned((c.g.Vh + bt1 - 1) / bt1);
+    const unsigned g1 = unsigned((n_links + bt1 - 1) / bt1);
 #define SUN_LAUNCH_VAR(K, V)                                                            \
   if (mode == kHeatbathMode) {                                                          \
     if (ru)                                                                             \
@@ -1763,7 +1859,7 @@ template <class R, int N, int S>
 cudaError_t launch_pair(const Ctx& c, int mode, int mu, uint32_t step_offset, uint32_t reunit_mod,
                         uint32_t reunit_rem) {
   const bool ru = reunit_mod != 0u;
-  bool two = !c.wave;
+  bool two = !c.wave || c.h_begin != 0 || c.h_end != c.g.Vh;  // a slab: its own pass ranges
   if constexpr (has_group<R, N>()) two = two || (!ru && use_group<R, N>(c.variant));
   if constexpr (has_variants<R, N, S>()) two = two || (c.variant & 18) != 0;
   if (two) {
@@ -1803,6 +1899,8 @@ inline LinkParams make_link_params(const Ctx& c, int hot) {
   p.g = c.g;
   p.key = make_uint2(uint32_t(c.seed & 0xffffffffu), uint32_t(c.seed >> 32));
   p.hot = hot;
+  p.lex_offset = c.lex_offset;
+  p.v_global = c.v_global;
   return p;
 }
 
@@ -1825,6 +1923,8 @@ inline ObsParams make_obs_params(const Ctx& c) {
   p.links = c.links;
   p.block_bytes = c.block_bytes;
   p.g = c.g;
+  p.h_begin = c.h_begin;
+  p.h_end = c.h_end;
   return p;
 }
 
@@ -1844,9 +1944,10 @@ cudaError_t launch_plaquette(const Ctx& c, double* out, const uint32_t* slot, in
   rp.cap = cap;
   rp.stride = c.obs_stride;
   rp.offset = c.obs_offset;
-  rp.scale = 1.0 / (6.0 * double(c.g.V) * N);
+  rp.scale = 1.0 / (6.0 * double(c.v_global) * N);
   const int bt = 256;
-  plaquette_kernel<R, N, S><<<reduce_grid(c, c.g.V, bt), bt, 0, c.stream>>>(make_obs_params(c), rp);
+  plaquette_kernel<R, N, S><<<reduce_grid(c, 2 * (c.h_end - c.h_begin), bt), bt, 0, c.stream>>>(make_obs_params(c),
+                                                                                                 rp);
   return cudaGetLastError();
 }
 
@@ -1864,6 +1965,34 @@ cudaError_t launch_polyakov(const Ctx& c, double* out, const uint32_t* slot, int
   rp.scale = 1.0 / (double(N) * double(nsp));
   const int bt = 128;
   polyakov_kernel<R, N, S><<<reduce_grid(c, nsp, bt), bt, 0, c.stream>>>(make_obs_params(c), rp);
+  return cudaGetLastError();
+}
+
+// a slab's partial Polyakov products over its interior slices [h_begin, h_end) / (Vs / 2)
+template <class R, int N, int S>
+cudaError_t launch_polyakov_partial(const Ctx& c, void* out) {
+  const int64_t nsp = int64_t(c.g.nx) * c.g.ny * c.g.nz;
+  const int64_t half_slice = nsp / 2;
+  polyakov_partial_kernel<R, N, S><<<unsigned((nsp + 127) / 128), 128, 0, c.stream>>>(
+      make_obs_params(c), int(c.h_begin / half_slice), int(c.h_end / half_slice), out);
+  return cudaGetLastError();
+}
+
+// the slabs' partial products (device array of n pointers) -> Polyakov loop
+template <class R, int N, int S>
+cudaError_t launch_polyakov_combine(const Ctx& c, const void* const* parts, int n, double* out, const uint32_t* slot,
+                                    int cap) {
+  ReduceParams rp;
+  rp.partials = c.partials + 2 * kMaxReduceBlocks;
+  rp.counter = &c.state->poly_counter;
+  rp.out = out;
+  rp.slot = slot;
+  rp.cap = cap;
+  rp.stride = c.obs_stride;
+  rp.offset = c.obs_offset;
+  const int64_t nsp = int64_t(c.g.nx) * c.g.ny * c.g.nz;
+  rp.scale = 1.0 / (double(N) * double(nsp));
+  polyakov_combine_kernel<R, N, S><<<reduce_grid(c, nsp, 128), 128, 0, c.stream>>>(parts, n, nsp, rp);
   return cudaGetLastError();
 }
 
@@ -1975,6 +2104,9 @@ const Ops* ops_instance() {
       &launch_reunit<R, N, S>,
       &launch_plaquette<R, N, S>,
       &launch_polyakov<R, N, S>,
+      &launch_polyakov_partial<R, N, S>,
+      &launch_polyakov_combine<R, N, S>,
+      sizeof(PolyPart<R, N, S>),
       &launch_export<R, N, S>,
       &launch_import<R, N, S>,
       has_batch<R, N, S>() ? &launch_batch_pass<R, N, S> : nullptr,

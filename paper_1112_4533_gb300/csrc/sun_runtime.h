@@ -68,6 +68,12 @@ struct Ctx {
   uint32_t* wave;  // kWaveSyncWords + Nt words of wavefront synchronisation
   int wave_lag;    // t-slices the even units of a wavefront run ahead of the odd ones
   uint32_t wave_skip;  // fault injection: leading units every wavefront launch leaves out (0 normally)
+  // A slab of a lattice cut into t-slabs (otherwise the whole lattice: [0, Vh),
+  // 0, V): passes and the plaquette cover half-sites [h_begin, h_end) of each
+  // parity, and local site lex is site (lex + lex_offset) mod v_global of the
+  // whole lattice (random numbers, re-unitarization runs, hot start).
+  int64_t h_begin, h_end;
+  uint32_t lex_offset, v_global;
 };
 
 // One chain (lattice) of a batch, as the batched kernels read it.
@@ -120,6 +126,12 @@ struct Ops {
   cudaError_t (*reunit)(const Ctx&);
   cudaError_t (*plaquette)(const Ctx&, double* out, const uint32_t* slot, int cap);
   cudaError_t (*polyakov)(const Ctx&, double* out, const uint32_t* slot, int cap);
+  // t-slabs: per-spatial-site products over a slab's interior slices, and their
+  // ordered product and trace over n slabs (the Polyakov loop of the whole lattice)
+  cudaError_t (*polyakov_partial)(const Ctx&, void* out);
+  cudaError_t (*polyakov_combine)(const Ctx&, const void* const* parts, int n, double* out, const uint32_t* slot,
+                                  int cap);
+  size_t polyakov_partial_bytes;  // per spatial site
   cudaError_t (*export_links)(const Ctx&, double* dst, int64_t first, int64_t count);
   cudaError_t (*import_links)(const Ctx&, const double* src, int64_t first, int64_t count);
   cudaError_t (*batch_pass)(const BatchCtx&, int mode, int mu, int parity, uint32_t step_offset, uint32_t reunit_mod,

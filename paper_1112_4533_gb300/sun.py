@@ -83,6 +83,12 @@ SIGNATURES = [
     ("sun_save_config", ctypes.c_int, [_P, ctypes.c_char_p]),
     ("sun_load_config", ctypes.c_int, [_P, ctypes.c_char_p]),
     ("sun_read_config_header", ctypes.c_int, [ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(ConfigHeader)]),
+    ("sun_slabs_create", ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _I4, ctypes.c_int, ctypes.c_double,
+                                        ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(Options)]),
+    ("sun_slabs_destroy", None, [_P]),
+    ("sun_slabs_run", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D]),
+    ("sun_slabs_export_links", ctypes.c_int, [_P, _D, ctypes.c_size_t]),
+    ("sun_slabs_import_links", ctypes.c_int, [_P, _D, ctypes.c_size_t]),
     ("sun_autotune", ctypes.c_int, [ctypes.c_int, _I4, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                     ctypes.POINTER(Options), _D]),
     ("sun_autotune_batch", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -404,3 +410,59 @@ class Batch:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Slabs:
+    """A lattice cut into n_slabs t-slabs with halo exchange after every pass
+    (sun_slabs_*): the same chain as one Lattice with the same seed."""
+
+    def __init__(self, nc, dims, n_slabs, beta, hot_start=False, seed=1, precision=32, storage=0, reunit_every=1,
+                 block_threads=0, use_graphs=True, variant=0, reunit_mode=0):
+        import torch  # streams only
+        self.nc = int(nc)
+        self.dims = tuple(int(d) for d in dims)
+        self.n_slabs = int(n_slabs)
+        self._lib = load_library()
+        self.stream = torch.cuda.Stream()
+        o = _options(precision, storage, reunit_every, block_threads, ctypes.c_void_p(self.stream.cuda_stream),
+                     None, 0, use_graphs, variant, reunit_mode)
+        h = ctypes.c_void_p()
+        _check(self._lib.sun_slabs_create(ctypes.byref(h), self.nc, _dims(dims), self.n_slabs, float(beta),
+                                          int(bool(hot_start)), int(seed), ctypes.byref(o)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.sun_slabs_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def run(self, n_sweeps, n_heatbath=1, n_overrelax=4, plaquette=True, polyakov=True):
+        plaq = np.zeros(n_sweeps) if plaquette else None
+        poly = np.zeros(2 * n_sweeps) if polyakov else None
+        _check(self._lib.sun_slabs_run(self._h, int(n_sweeps), int(n_heatbath), int(n_overrelax),
+                                       _dptr(plaq) if plaquette else None, _dptr(poly) if polyakov else None))
+        return plaq, (poly[0::2] + 1j * poly[1::2]) if polyakov else None
+
+    def export_links(self):
+        nx, ny, nz, nt = self.dims
+        out = np.empty((4, nt, nz, ny, nx, self.nc, self.nc), dtype=np.complex128)
+        flat = out.view(np.float64).reshape(-1)
+        _check(self._lib.sun_slabs_export_links(self._h, _dptr(flat), flat.size))
+        return out
+
+    def import_links(self, U):
+        a = np.ascontiguousarray(U, dtype=np.complex128)
+        flat = a.view(np.float64).reshape(-1)
+        _check(self._lib.sun_slabs_import_links(self._h, _dptr(flat), flat.size))

@@ -126,3 +126,14 @@ def test_wavefront_options_validated_on_the_host(lib):
         o = sun._options()
         setattr(o, field, bad)
         assert lib.sun_lattice_create(ctypes.byref(h), 3, _dims((4, 4, 4, 4)), 6.0, 0, 1, ctypes.byref(o)) == 1
+
+
+def test_slab_arguments_rejected_on_the_host(lib):
+    from paper_1112_4533_gb300 import sun
+    h = ctypes.c_void_p()
+    o = sun._options()
+    # Nt = 8: 3 slabs do not divide it, 8 slabs would be 1 slice thick (odd), 0 slabs is no decomposition
+    for n in (3, 8, 0):
+        assert lib.sun_slabs_create(ctypes.byref(h), 3, _dims((4, 4, 4, 8)), n, 6.0, 0, 1, ctypes.byref(o)) == 1
+    o.device_buf = ctypes.c_void_p(4096)
+    assert lib.sun_slabs_create(ctypes.byref(h), 3, _dims((4, 4, 4, 8)), 2, 6.0, 0, 1, ctypes.byref(o)) == 1
