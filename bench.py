@@ -12,8 +12,9 @@ hot path).
   value      link updates/s, device-resident lattice (2.0 GB, larger than L2),
              CUDA events on the lattice's stream, max over ranks
   e2e        the same metric through the C ABI with host buffers: every step
-             imports the configuration from pinned host memory, sweeps,
-             reads the observables and exports the configuration back
+             imports the configuration from pinned host memory (compact
+             format: the stored rows in FP32, 2.04 GB), sweeps, reads the
+             observables and exports the configuration back
   roofline   the dominant kernel (overrelaxation pass): algorithmic bytes
              (8 link reads + 1 link write per update) / measured launch time
   cpu_baseline  the FP64 CPU oracle on a bounded sample of the same workload
@@ -420,34 +421,36 @@ def gpu_arm(args):
             torch.cuda.empty_cache()
         L = sun.Lattice(NC, DIMS, BETA, hot_start=False, seed=1 + rank, storage=args.storage, **kw)
 
-    # ---- end to end through the C ABI with pinned host buffers
+    # ---- end to end through the C ABI with pinned host buffers: every step the
+    # configuration comes from and goes back to host memory in the compact format
+    # (the stored rows in FP32, as configuration files hold them)
     e2e = None
     if not args.no_e2e:
-        n_doubles = 8 * NC * NC * V
-        host_a = torch.empty(n_doubles, dtype=torch.float64).pin_memory()
-        host_b = torch.empty(n_doubles, dtype=torch.float64).pin_memory()
-        L.export_links_raw(host_a.data_ptr(), n_doubles)
+        nbytes = L.links_bytes
+        host_a = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+        host_b = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+        L.export_stored_raw(host_a.data_ptr(), nbytes)
         ke = max(2, min(K, args.e2e_steps))
         for _ in range(1):
-            L.import_links_raw(host_a.data_ptr(), n_doubles)
+            L.import_stored_raw(host_a.data_ptr(), nbytes)
             L.run(1, N_HB, N_OR)
-            L.export_links_raw(host_b.data_ptr(), n_doubles)
+            L.export_stored_raw(host_b.data_ptr(), nbytes)
         barrier(world)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for s in range(ke):
             src, dst = (host_a, host_b) if s % 2 == 0 else (host_b, host_a)
-            L.import_links_raw(src.data_ptr(), n_doubles)
+            L.import_stored_raw(src.data_ptr(), nbytes)
             L.run(1, N_HB, N_OR)
-            L.export_links_raw(dst.data_ptr(), n_doubles)
+            L.export_stored_raw(dst.data_ptr(), nbytes)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         dt = allreduce_max(dt, world)
         e2e = {"value": updates_per_sweep() * ke * world / dt, "unit": METRIC,
-               "h2d_bytes_per_step": n_doubles * 8, "d2h_bytes_per_step": n_doubles * 8 + 3 * 8,
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 3 * 8,
                "steps": ke, "ms_per_step": dt / ke * 1e3,
-               "path": "sun_import_links + sun_run(1 sweep, observables to host) + sun_export_links, "
-                       "canonical FP64 links in pinned host memory"}
+               "path": "sun_import_stored + sun_run(1 sweep, observables to host) + sun_export_stored: the "
+                       "configuration in pinned host memory in the compact format (stored rows, FP32)"}
         del host_a, host_b
 
     cpu = None

@@ -189,6 +189,17 @@ sun_status sun_polyakov_loop(sun_lattice* lat, double* re, double* im);
 sun_status sun_export_links(sun_lattice* lat, double* host, size_t n_doubles);
 sun_status sun_import_links(sun_lattice* lat, const double* host, size_t n_doubles);
 
+/* The compact host format: for every link in canonical order the rows
+ * 0 .. storage/(2 Nc) - 1 that the storage format keeps, as (re, im) pairs in
+ * the lattice's precision (the payload of configuration files): 4V x stored link
+ * bytes (sun_lattice_info.links_bytes).  Exact both ways: the stored values
+ * themselves.  SU(2) quaternion storage: row 0 = (a0 + i a3, a2 + i a1).  The
+ * buffer must be 16-byte aligned; page-locked host memory is read or written
+ * directly by the conversion kernel, pageable memory goes through the staging
+ * buffer.  Both sync. */
+sun_status sun_export_stored(sun_lattice* lat, void* host, size_t bytes);
+sun_status sun_import_stored(sun_lattice* lat, const void* host, size_t bytes);
+
 /* Random state: the heatbath step counter (the seed is fixed at creation). */
 sun_status sun_get_heatbath_step(sun_lattice* lat, uint64_t* step); /* syncs */
 sun_status sun_set_heatbath_step(sun_lattice* lat, uint64_t step);

@@ -625,6 +625,41 @@ sun_status sun_import_links(sun_lattice* L, const double* host, size_t n) {
   return SUN_OK;
 }
 
+// The compact host format (stored rows in the storage precision): 4V x link_bytes.
+static sun_status copy_stored(sun_lattice* L, void* host, size_t bytes, bool to_host) {
+  if (!L || !host) return fail(SUN_ERR_ARG, "NULL argument");
+  if (bytes != L->plan.links_bytes)
+    return fail(SUN_ERR_ARG, "host buffer holds %zu bytes, need %zu", bytes, L->plan.links_bytes);
+  if (reinterpret_cast<uintptr_t>(host) % 16) return fail(SUN_ERR_ARG, "host buffer must be 16-byte aligned");
+  SUN_TRY(set_device(L));
+  const sun::Ctx c = ctx_on(L, L->stream);
+  const int64_t total = 4 * L->ctx.g.V, lb = L->ops->link_bytes;
+  char* h = static_cast<char*>(host);
+  if (double* dev = mapped_host(host)) {
+    SUN_TRY(check_launch(to_host ? L->ops->export_stored(c, dev, 0, total) : L->ops->import_stored(c, dev, 0, total),
+                         to_host ? "export" : "import"));
+  } else {
+    for (int64_t first = 0; first < total; first += L->plan.staging_links) {
+      const int64_t cnt = std::min<int64_t>(total - first, L->plan.staging_links);
+      if (to_host) {
+        SUN_TRY(check_launch(L->ops->export_stored(c, L->staging, first, cnt), "export"));
+        SUN_CUDA(cudaMemcpyAsync(h + first * lb, L->staging, size_t(cnt * lb), cudaMemcpyDeviceToHost, L->stream));
+      } else {
+        SUN_CUDA(cudaMemcpyAsync(L->staging, h + first * lb, size_t(cnt * lb), cudaMemcpyHostToDevice, L->stream));
+        SUN_TRY(check_launch(L->ops->import_stored(c, L->staging, first, cnt), "import"));
+      }
+    }
+  }
+  SUN_CUDA(cudaStreamSynchronize(L->stream));
+  return SUN_OK;
+}
+
+sun_status sun_export_stored(sun_lattice* L, void* host, size_t bytes) { return copy_stored(L, host, bytes, true); }
+
+sun_status sun_import_stored(sun_lattice* L, const void* host, size_t bytes) {
+  return copy_stored(L, const_cast<void*>(host), bytes, false);
+}
+
 sun_status sun_get_heatbath_step(sun_lattice* L, uint64_t* step) {
   if (!L || !step) return fail(SUN_ERR_ARG, "NULL argument");
   SUN_TRY(set_device(L));
@@ -748,39 +783,25 @@ sun_status sun_save_config(sun_lattice* L, const char* path) {
   h.seed = L->seed;
   h.heatbath_step = step;
   h.sweeps_done = L->sweeps_done;
-  const int nc = L->nc, rows = stored_rows(nc, L->storage), per = 2 * nc * nc, vals = 2 * nc * rows;
   const int64_t total = 4 * L->ctx.g.V;
-  const size_t vbytes = size_t(L->precision / 8);
-  h.payload_bytes = uint64_t(total) * uint64_t(vals) * vbytes;
+  // rows storage / (2 Nc) of Nc complex values in the storage precision = the stored link bytes
+  h.payload_bytes = uint64_t(total) * uint64_t(L->ops->link_bytes);
   File F;
   F.f = fopen(path, "wb");
   if (!F.f) return fail(SUN_ERR_ARG, "cannot create %s", path);
   if (fwrite(kConfigMagic, 1, 8, F.f) != 8 || fwrite(&h, sizeof(h), 1, F.f) != 1)
     return fail(SUN_ERR_ARG, "write to %s failed", path);
   const sun::Ctx c = ctx_on(L, L->stream);
-  std::vector<double> canon(size_t(L->plan.staging_links) * size_t(per));
-  std::vector<unsigned char> out(size_t(L->plan.staging_links) * size_t(vals) * vbytes);
+  // the payload is the compact format: the stored rows in the storage precision
+  const int64_t lb = L->ops->link_bytes;
+  std::vector<unsigned char> out(size_t(L->plan.staging_links) * size_t(lb));
   uint64_t sum = kFnvBasis;
   for (int64_t first = 0; first < total; first += L->plan.staging_links) {
     const int64_t cnt = std::min<int64_t>(total - first, L->plan.staging_links);
-    SUN_TRY(check_launch(L->ops->export_links(c, L->staging, first, cnt), "export"));
-    SUN_CUDA(cudaMemcpyAsync(canon.data(), L->staging, size_t(cnt * per) * sizeof(double), cudaMemcpyDeviceToHost,
-                             L->stream));
+    SUN_TRY(check_launch(L->ops->export_stored(c, L->staging, first, cnt), "export"));
+    SUN_CUDA(cudaMemcpyAsync(out.data(), L->staging, size_t(cnt * lb), cudaMemcpyDeviceToHost, L->stream));
     SUN_CUDA(cudaStreamSynchronize(L->stream));
-    // the stored rows of each link, in the lattice's precision (exact for FP32 links)
-    for (int64_t l = 0; l < cnt; ++l) {
-      const double* src = canon.data() + l * per;
-      unsigned char* dst = out.data() + size_t(l) * size_t(vals) * vbytes;
-      for (int k = 0; k < vals; ++k) {
-        if (vbytes == 4) {
-          const float v = float(src[k]);
-          std::memcpy(dst + 4 * k, &v, 4);
-        } else {
-          std::memcpy(dst + 8 * k, &src[k], 8);
-        }
-      }
-    }
-    const size_t nbytes = size_t(cnt) * size_t(vals) * vbytes;
+    const size_t nbytes = size_t(cnt * lb);
     sum = fnv1a_words(sum, out.data(), nbytes);
     if (fwrite(out.data(), 1, nbytes, F.f) != nbytes) return fail(SUN_ERR_ARG, "write to %s failed", path);
   }
@@ -809,35 +830,18 @@ sun_status sun_load_config(sun_lattice* L, const char* path) {
   File F;
   F.f = fopen(path, "rb");
   if (!F.f || fseek(F.f, 128, SEEK_SET) != 0) return fail(SUN_ERR_ARG, "cannot read %s", path);
-  const int nc = L->nc, rows = stored_rows(nc, L->storage), per = 2 * nc * nc, vals = 2 * nc * rows;
   const int64_t total = 4 * L->ctx.g.V;
-  const size_t vbytes = size_t(L->precision / 8);
   const sun::Ctx c = ctx_on(L, L->stream);
-  std::vector<double> canon(size_t(L->plan.staging_links) * size_t(per), 0.0);
-  std::vector<unsigned char> in(size_t(L->plan.staging_links) * size_t(vals) * vbytes);
+  const int64_t lb = L->ops->link_bytes;
+  std::vector<unsigned char> in(size_t(L->plan.staging_links) * size_t(lb));
   SUN_CUDA(cudaStreamSynchronize(L->stream));
   for (int64_t first = 0; first < total; first += L->plan.staging_links) {
     const int64_t cnt = std::min<int64_t>(total - first, L->plan.staging_links);
-    const size_t nbytes = size_t(cnt) * size_t(vals) * vbytes;
+    const size_t nbytes = size_t(cnt * lb);
     if (fread(in.data(), 1, nbytes, F.f) != nbytes) return fail(SUN_ERR_ARG, "%s: short read", path);
-    for (int64_t l = 0; l < cnt; ++l) {
-      const unsigned char* src = in.data() + size_t(l) * size_t(vals) * vbytes;
-      double* dst = canon.data() + l * per;
-      for (int k = 0; k < vals; ++k) {
-        if (vbytes == 4) {
-          float v;
-          std::memcpy(&v, src + 4 * k, 4);
-          dst[k] = double(v);
-        } else {
-          std::memcpy(&dst[k], src + 8 * k, 8);
-        }
-      }
-    }
-    SUN_CUDA(cudaMemcpyAsync(L->staging, canon.data(), size_t(cnt * per) * sizeof(double), cudaMemcpyHostToDevice,
-                             L->stream));
-    SUN_TRY(check_launch(L->ops->import_links(c, L->staging, first, cnt), "import"));
-    // the pageable source buffer is reused by the next chunk
-    SUN_CUDA(cudaStreamSynchronize(L->stream));
+    SUN_CUDA(cudaMemcpyAsync(L->staging, in.data(), nbytes, cudaMemcpyHostToDevice, L->stream));
+    SUN_TRY(check_launch(L->ops->import_stored(c, L->staging, first, cnt), "import"));
+    SUN_CUDA(cudaStreamSynchronize(L->stream));  // the host buffer is reused
   }
   // the chain state: graphs captured with the old seed or beta are dropped
   if (h.seed != L->seed || h.beta != L->beta) {

@@ -1711,6 +1711,95 @@ __global__ void __launch_bounds__(128) import_kernel(const ObsParams p, const do
   }
 }
 
+// The compact host format: the stored rows (rows 0 .. NR / (2 Nc) - 1) of every
+// link as (re, im) pairs in canonical link order, in the storage precision.  For
+// quaternion storage that is row 0 = (a0 + i a3, a2 + i a1).  Staged through
+// shared memory so that host memory is read and written in 8-byte words.
+template <class R, int N, int S>
+__device__ __forceinline__ void stored_to_rows(const R (&r)[Layout<R, N, S>::nreals], R* o) {
+  constexpr int NR = Layout<R, N, S>::nreals;
+  if constexpr (S == kQuat) {
+    o[0] = r[0];
+    o[1] = r[3];
+    o[2] = r[2];
+    o[3] = r[1];
+  } else {
+#pragma unroll
+    for (int k = 0; k < NR; ++k) o[k] = r[k];
+  }
+}
+
+template <class R, int N, int S>
+__device__ __forceinline__ void rows_to_stored(const R* o, R (&r)[Layout<R, N, S>::nreals]) {
+  constexpr int NR = Layout<R, N, S>::nreals;
+  if constexpr (S == kQuat) {
+    r[0] = o[0];
+    r[3] = o[1];
+    r[2] = o[2];
+    r[1] = o[3];
+  } else {
+#pragma unroll
+    for (int k = 0; k < NR; ++k) r[k] = o[k];
+  }
+}
+
+// links per block of the compact conversion kernels: up to 512, within 48 KB of
+// shared memory (a multiple of 16 links: block offsets stay 16-byte aligned)
+template <class R, int N, int S>
+__host__ __device__ constexpr int compact_links_per_block() {
+  return (48 * 1024 / Layout<R, N, S>::bytes) >= 512 ? 512 : ((48 * 1024 / Layout<R, N, S>::bytes) / 16) * 16;
+}
+
+// n bytes (a multiple of 8) between 16-byte aligned addresses: 16-byte words,
+// then one 8-byte word if left
+__device__ __forceinline__ void copy_words(void* dst, const void* src, int n) {
+  uint4* d = static_cast<uint4*>(dst);
+  const uint4* s = static_cast<const uint4*>(src);
+  const int w16 = n / 16;
+  for (int j = threadIdx.x; j < w16; j += blockDim.x) d[j] = s[j];
+  if ((n & 15) && threadIdx.x == 0)
+    reinterpret_cast<unsigned long long*>(d + w16)[0] = reinterpret_cast<const unsigned long long*>(s + w16)[0];
+}
+
+template <class R, int N, int S>
+__global__ void __launch_bounds__(256) export_stored_kernel(const ObsParams p, R* dst, int64_t first, int64_t count) {
+  constexpr int NR = Layout<R, N, S>::nreals;
+  constexpr int LPB = compact_links_per_block<R, N, S>();
+  __shared__ __align__(16) R sm[LPB * NR];
+  const int64_t rel0 = int64_t(blockIdx.x) * LPB;
+  const int nl = int((count - rel0) < LPB ? (count - rel0) : LPB);
+  for (int i = threadIdx.x; i < nl; i += blockDim.x) {
+    const int64_t l = first + rel0 + i;
+    const int mu = int(l / p.g.V);
+    const int64_t lex = l - int64_t(mu) * p.g.V;
+    R r[NR];
+    load_reals<R, NR, kLoadNc>(obs_block(p, mu, link_parity(p.g, lex)), p.g.Vh, lex >> 1, r);
+    stored_to_rows<R, N, S>(r, sm + i * NR);
+  }
+  __syncthreads();
+  copy_words(dst + rel0 * NR, sm, nl * NR * int(sizeof(R)));
+}
+
+template <class R, int N, int S>
+__global__ void __launch_bounds__(256) import_stored_kernel(const ObsParams p, const R* src, int64_t first,
+                                                            int64_t count) {
+  constexpr int NR = Layout<R, N, S>::nreals;
+  constexpr int LPB = compact_links_per_block<R, N, S>();
+  __shared__ __align__(16) R sm[LPB * NR];
+  const int64_t rel0 = int64_t(blockIdx.x) * LPB;
+  const int nl = int((count - rel0) < LPB ? (count - rel0) : LPB);
+  copy_words(sm, src + rel0 * NR, nl * NR * int(sizeof(R)));
+  __syncthreads();
+  for (int i = threadIdx.x; i < nl; i += blockDim.x) {
+    const int64_t l = first + rel0 + i;
+    const int mu = int(l / p.g.V);
+    const int64_t lex = l - int64_t(mu) * p.g.V;
+    R r[NR];
+    rows_to_stored<R, N, S>(sm + i * NR, r);
+    store_reals<R, NR>(const_cast<char*>(obs_block(p, mu, link_parity(p.g, lex))), p.g.Vh, lex >> 1, r);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Host launchers and the operation table
 // ---------------------------------------------------------------------------
@@ -2005,6 +2094,24 @@ cudaError_t launch_export(const Ctx& c, double* dst, int64_t first, int64_t coun
 }
 
 template <class R, int N, int S>
+cudaError_t launch_export_stored(const Ctx& c, void* dst, int64_t first, int64_t count) {
+  if (count <= 0) return cudaSuccess;
+  constexpr int LPB = compact_links_per_block<R, N, S>();
+  export_stored_kernel<R, N, S><<<unsigned((count + LPB - 1) / LPB), 256, 0, c.stream>>>(
+      make_obs_params(c), static_cast<R*>(dst), first, count);
+  return cudaGetLastError();
+}
+
+template <class R, int N, int S>
+cudaError_t launch_import_stored(const Ctx& c, const void* src, int64_t first, int64_t count) {
+  if (count <= 0) return cudaSuccess;
+  constexpr int LPB = compact_links_per_block<R, N, S>();
+  import_stored_kernel<R, N, S><<<unsigned((count + LPB - 1) / LPB), 256, 0, c.stream>>>(
+      make_obs_params(c), static_cast<const R*>(src), first, count);
+  return cudaGetLastError();
+}
+
+template <class R, int N, int S>
 cudaError_t launch_import(const Ctx& c, const double* src, int64_t first, int64_t count) {
   if (count <= 0) return cudaSuccess;
   constexpr int LPB = conv_links_per_block<N>();
@@ -2109,6 +2216,8 @@ const Ops* ops_instance() {
       sizeof(PolyPart<R, N, S>),
       &launch_export<R, N, S>,
       &launch_import<R, N, S>,
+      &launch_export_stored<R, N, S>,
+      &launch_import_stored<R, N, S>,
       has_batch<R, N, S>() ? &launch_batch_pass<R, N, S> : nullptr,
       has_batch<R, N, S>() ? &launch_batch_reunit<R, N, S> : nullptr,
       has_batch<R, N, S>() ? &launch_batch_plaquette<R, N, S> : nullptr,

@@ -134,6 +134,9 @@ struct Ops {
   size_t polyakov_partial_bytes;  // per spatial site
   cudaError_t (*export_links)(const Ctx&, double* dst, int64_t first, int64_t count);
   cudaError_t (*import_links)(const Ctx&, const double* src, int64_t first, int64_t count);
+  // the compact host format: stored rows in the storage precision, canonical order
+  cudaError_t (*export_stored)(const Ctx&, void* dst, int64_t first, int64_t count);
+  cudaError_t (*import_stored)(const Ctx&, const void* src, int64_t first, int64_t count);
   cudaError_t (*batch_pass)(const BatchCtx&, int mode, int mu, int parity, uint32_t step_offset, uint32_t reunit_mod,
                             uint32_t reunit_rem);
   cudaError_t (*batch_reunit)(const BatchCtx&);

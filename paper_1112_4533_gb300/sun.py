@@ -80,6 +80,8 @@ SIGNATURES = [
     ("sun_batch_create", ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int, _P, ctypes.c_int]),
     ("sun_batch_run", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D]),
     ("sun_batch_destroy", None, [_P]),
+    ("sun_export_stored", ctypes.c_int, [_P, _P, ctypes.c_size_t]),
+    ("sun_import_stored", ctypes.c_int, [_P, _P, ctypes.c_size_t]),
     ("sun_save_config", ctypes.c_int, [_P, ctypes.c_char_p]),
     ("sun_load_config", ctypes.c_int, [_P, ctypes.c_char_p]),
     ("sun_read_config_header", ctypes.c_int, [ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(ConfigHeader)]),
@@ -340,6 +342,24 @@ class Lattice:
     @heatbath_step.setter
     def heatbath_step(self, step):
         _check(self._lib.sun_set_heatbath_step(self.handle, int(step)))
+
+    def export_stored(self, out=None):
+        """The compact host format (sun_export_stored): a uint8 array of links_bytes."""
+        if out is None:
+            out = np.empty(self.links_bytes, dtype=np.uint8)
+        assert out.flags.c_contiguous and out.nbytes == self.links_bytes
+        _check(self._lib.sun_export_stored(self.handle, out.ctypes.data_as(ctypes.c_void_p), out.nbytes))
+        return out
+
+    def import_stored(self, buf):
+        a = np.ascontiguousarray(buf).view(np.uint8).reshape(-1)
+        _check(self._lib.sun_import_stored(self.handle, a.ctypes.data_as(ctypes.c_void_p), a.nbytes))
+
+    def export_stored_raw(self, host_ptr, nbytes):
+        _check(self._lib.sun_export_stored(self.handle, ctypes.c_void_p(host_ptr), int(nbytes)))
+
+    def import_stored_raw(self, host_ptr, nbytes):
+        _check(self._lib.sun_import_stored(self.handle, ctypes.c_void_p(host_ptr), int(nbytes)))
 
     def save(self, path):
         """Write links and chain state to a configuration file (sun_save_config)."""

@@ -79,3 +79,29 @@ def test_damaged_file_leaves_the_lattice_unchanged(sunlib, tmp_path):
         with pytest.raises(sunlib.SunError):
             B.load(path)
         assert np.array_equal(B.export_links(), before) and B.heatbath_step == step
+
+
+@pytest.mark.parametrize("nc,st,prec", CASES)
+def test_compact_host_format(sunlib, nc, st, prec):
+    """sun_export_stored: the stored rows of the canonical export in the storage
+    precision; pinned and pageable buffers agree; the round trip is exact."""
+    import torch
+    dims = (4, 4, 4, 6)
+    rows = st // (2 * nc)
+    with sunlib.Lattice(nc, dims, beta_for(nc), hot_start=True, seed=8, storage=st, precision=prec) as L:
+        L.run(1, 1, 1)
+        U = L.export_links()
+        raw = L.export_stored()
+        vals = raw.view(np.float32 if prec == 32 else np.float64).reshape(4, dims[3], dims[2], dims[1], dims[0],
+                                                                          rows, nc, 2)
+        want = np.stack([U[..., :rows, :].real, U[..., :rows, :].imag], axis=-1)
+        assert np.array_equal(vals, want.astype(vals.dtype))
+        pinned = torch.empty(raw.nbytes, dtype=torch.uint8).pin_memory()
+        L.export_stored_raw(pinned.data_ptr(), raw.nbytes)
+        assert np.array_equal(pinned.numpy(), raw)
+        L.run(1, 1, 1)  # move away, then restore from each buffer
+        L.import_stored(raw)
+        assert np.array_equal(L.export_links(), U)
+        L.run(1, 1, 1)
+        L.import_stored_raw(pinned.data_ptr(), raw.nbytes)
+        assert np.array_equal(L.export_links(), U)
