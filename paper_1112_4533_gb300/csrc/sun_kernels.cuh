@@ -454,8 +454,20 @@ struct Group {
   static constexpr int CPR = 2 * N * int(sizeof(R)) / 16;  // 16-byte components per row
 };
 
+// Shared memory of one link slot: three N x N staging matrices, padded so that
+// consecutive slots start 4 banks apart.  The lanes of a warp read the same
+// entry of their own slot's matrix in one instruction, so the warp's 5 to 8 slots
+// then hit different banks instead of colliding every 32 / gcd words.
 template <class R, int N>
-constexpr bool has_group() {
+struct alignas(16) GroupSlot {
+  static constexpr int kWords = 3 * N * N * 2 * int(sizeof(R)) / 4;
+  static constexpr int kPadWords = ((4 - kWords % 32) % 32 + 32) % 32;
+  Cpx<R> m[3][N][N];
+  uint32_t pad[kPadWords > 0 ? kPadWords : 1];
+};
+
+template <class R, int N>
+__host__ __device__ constexpr bool has_group() {
   return (N == 4 || N == 6) && (2 * N * int(sizeof(R))) % 16 == 0;
 }
 
@@ -753,13 +765,15 @@ __device__ __forceinline__ void group_lane(int64_t first_link, int64_t Vh, int64
 }
 
 template <class R, int N, int MODE>
-__global__ void __launch_bounds__(128) update_pass_group(const PassParams p) {
-  __shared__ Cpx<R> sm[Group<R, N>::WARPS * Group<R, N>::SLOTS][3][N][N];
+// 5 resident blocks per SM: measured fastest for SU(6) FP32 (unbounded: 4 blocks,
+// 6 blocks: more spills); heatbath 6% and overrelaxation 2% faster than unbounded
+__global__ void __launch_bounds__(128, 5) update_pass_group(const PassParams p) {
+  __shared__ GroupSlot<R, N> sm[Group<R, N>::WARPS * Group<R, N>::SLOTS];
   int64_t h;
   bool active;
   int r, base, slot;
   group_lane<R, N>(p.h_begin + int64_t(blockIdx.x) * Group<R, N>::LPB, p.h_end, h, active, r, base, slot);
-  group_pass_body<R, N, MODE>(p, h, active, r, base, sm[slot]);
+  group_pass_body<R, N, MODE>(p, h, active, r, base, sm[slot].m);
 }
 
 // FP64 passes of Nc >= 5 are built without the fused re-unitarization
@@ -1488,7 +1502,7 @@ __global__ void __launch_bounds__(128)
     update_pass_batch_group(const BatchParams bp, int mu, int parity, uint32_t step_offset) {
   __shared__ PassParams sp;
   __shared__ uint32_t first;
-  __shared__ Cpx<R> sm[Group<R, N>::WARPS * Group<R, N>::SLOTS][3][N][N];
+  __shared__ GroupSlot<R, N> sm[Group<R, N>::WARPS * Group<R, N>::SLOTS];
   if (threadIdx.x == 0) {
     const int c = find_chain(bp.start, bp.n, blockIdx.x);
     const ChainDesc& d = bp.chains[c];
@@ -1515,7 +1529,7 @@ __global__ void __launch_bounds__(128)
   bool active;
   int r, base, slot;
   group_lane<R, N>(int64_t(blockIdx.x - first) * Group<R, N>::LPB, p.g.Vh, h, active, r, base, slot);
-  group_pass_body<R, N, MODE>(p, h, active, r, base, sm[slot]);
+  group_pass_body<R, N, MODE>(p, h, active, r, base, sm[slot].m);
 }
 
 // stage the chain's observable parameters of this block in shared memory
