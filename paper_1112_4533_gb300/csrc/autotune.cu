@@ -181,9 +181,14 @@ sun_status autotune(const std::vector<Spec>& specs, int n_hb, int n_or, int flag
     int variant, block;
   };
   std::vector<Shape> shapes = {{0, 64}, {0, 128}, {0, 256}};
+  // a batch of chains that do not fill the GPU alone runs the packed batch kernels,
+  // which have neither the packed-FP32 nor the wavefront form
+  bool own_launches = specs.size() == 1;
+  for (const Spec& s : specs)
+    if (s.nc >= 4 && int64_t(s.dims[0]) * s.dims[1] * s.dims[2] * s.dims[3] >= (int64_t(1) << 18)) own_launches = true;
   if (same_nc && nc0 == 3 && fp32) {
     shapes.push_back({1, 128});
-    shapes.push_back({17, 128});  // packed-FP32 overrelaxation, register-bounded heatbath
+    if (own_launches) shapes.push_back({17, 128});  // packed-FP32 overrelaxation, register-bounded heatbath
     if (flags & SUN_TUNE_TWO_ROW) {
       shapes.push_back({3, 128});
       shapes.push_back({2, 128});
@@ -228,11 +233,7 @@ sun_status autotune(const std::vector<Spec>& specs, int n_hb, int n_or, int flag
           best, best_ms);
 
   // 4. even/odd wavefront launches: only for kernels with that form, and in a
-  //    batch only where a chain runs its own launches (Nc >= 4 chains that fill
-  //    the GPU; the packed kernels of a batch have no wavefront form)
-  bool own_launches = specs.size() == 1;
-  for (const Spec& s : specs)
-    if (s.nc >= 4 && int64_t(s.dims[0]) * s.dims[1] * s.dims[2] * s.dims[3] >= (int64_t(1) << 18)) own_launches = true;
+  //    batch only where a chain runs its own launches
   const bool has_wave = own_launches && !(best.variant & 18) && !(same_nc && nc0 == 6 && !(best.variant & 4)) &&
                         !(same_nc && nc0 == 4 && (best.variant & 4));
   if (has_wave)

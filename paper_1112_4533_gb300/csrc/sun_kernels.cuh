@@ -1348,11 +1348,11 @@ __device__ __forceinline__ void site_polyakov(const ObsParams& p, int64_t xs, do
 template <class R, int N, int S>
 __global__ void __launch_bounds__(256) plaquette_kernel(const ObsParams p, const ReduceParams rp) {
   double acc[1] = {0.0};
-  const int64_t cnt = p.h_end - p.h_begin;  // sites per parity (all of them: Vh)
-  for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < 2 * cnt;
-       idx += int64_t(gridDim.x) * blockDim.x) {
+  // sites per parity: all of them (Vh) or a slab's interior; 32-bit site arithmetic
+  const uint32_t cnt = uint32_t(p.h_end - p.h_begin), h0 = uint32_t(p.h_begin);
+  for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < 2 * cnt; idx += gridDim.x * blockDim.x) {
     const int par = idx >= cnt ? 1 : 0;
-    acc[0] += site_plaquette<R, N, S>(p, par, p.h_begin + idx - par * cnt);
+    acc[0] += site_plaquette<R, N, S>(p, par, int64_t(h0 + idx - uint32_t(par) * cnt));
   }
   reduce_finish<1>(acc, rp);
 }
