@@ -1345,14 +1345,29 @@ __device__ __forceinline__ void site_polyakov(const ObsParams& p, int64_t xs, do
 }
 
 // <P> of one lattice: grid-stride over sites, deterministic FP64 reduction.
+// The whole lattice: sites idx < V in parity-block order.  (A loop over a
+// sub-range here costs SU(6) its register allocation: a kernel of its own does
+// the slabs.)
 template <class R, int N, int S>
 __global__ void __launch_bounds__(256) plaquette_kernel(const ObsParams p, const ReduceParams rp) {
   double acc[1] = {0.0};
-  // sites per parity: all of them (Vh) or a slab's interior; 32-bit site arithmetic
-  const uint32_t cnt = uint32_t(p.h_end - p.h_begin), h0 = uint32_t(p.h_begin);
-  for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < 2 * cnt; idx += gridDim.x * blockDim.x) {
+  for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < p.g.V;
+       idx += int64_t(gridDim.x) * blockDim.x) {
+    const int par = idx >= p.g.Vh ? 1 : 0;
+    acc[0] += site_plaquette<R, N, S>(p, par, idx - par * p.g.Vh);
+  }
+  reduce_finish<1>(acc, rp);
+}
+
+// A slab's interior: half-sites [h_begin, h_end) of each parity.
+template <class R, int N, int S>
+__global__ void __launch_bounds__(256) plaquette_slab_kernel(const ObsParams p, const ReduceParams rp) {
+  double acc[1] = {0.0};
+  const int64_t cnt = p.h_end - p.h_begin;
+  for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < 2 * cnt;
+       idx += int64_t(gridDim.x) * blockDim.x) {
     const int par = idx >= cnt ? 1 : 0;
-    acc[0] += site_plaquette<R, N, S>(p, par, int64_t(h0 + idx - uint32_t(par) * cnt));
+    acc[0] += site_plaquette<R, N, S>(p, par, p.h_begin + idx - par * cnt);
   }
   reduce_finish<1>(acc, rp);
 }
@@ -2049,8 +2064,11 @@ cudaError_t launch_plaquette(const Ctx& c, double* out, const uint32_t* slot, in
   rp.offset = c.obs_offset;
   rp.scale = 1.0 / (6.0 * double(c.v_global) * N);
   const int bt = 256;
-  plaquette_kernel<R, N, S><<<reduce_grid(c, 2 * (c.h_end - c.h_begin), bt), bt, 0, c.stream>>>(make_obs_params(c),
-                                                                                                 rp);
+  if (c.h_begin == 0 && c.h_end == c.g.Vh)
+    plaquette_kernel<R, N, S><<<reduce_grid(c, c.g.V, bt), bt, 0, c.stream>>>(make_obs_params(c), rp);
+  else
+    plaquette_slab_kernel<R, N, S><<<reduce_grid(c, 2 * (c.h_end - c.h_begin), bt), bt, 0, c.stream>>>(
+        make_obs_params(c), rp);
   return cudaGetLastError();
 }
 
