@@ -189,6 +189,14 @@ sun_status sun_polyakov_loop(sun_lattice* lat, double* re, double* im);
 sun_status sun_export_links(sun_lattice* lat, double* host, size_t n_doubles);
 sun_status sun_import_links(sun_lattice* lat, const double* host, size_t n_doubles);
 
+/* Health of the links (no counterpart in the paper; a diagnostic): over all 4V
+ * stored links, in FP64 of the stored values (two-row storage: with the
+ * rebuilt third row), the largest entry |(U U^+ - 1)_ij|, the largest
+ * |det U - 1|, and the number of links with a NaN or infinite entry (those are
+ * left out of the two maxima).  Syncs. */
+sun_status sun_check_links(sun_lattice* lat, double* max_unitarity_dev, double* max_det_dev,
+                           uint64_t* nonfinite);
+
 /* The compact host format: for every link in canonical order the rows
  * 0 .. storage/(2 Nc) - 1 that the storage format keeps, as (re, im) pairs in
  * the lattice's precision (the payload of configuration files): 4V x stored link
@@ -347,8 +355,10 @@ enum {
  * those are not tuned; on success the fastest configuration is written back
  * into *opt (block_threads, variant, and the tuned fields) and, if
  * ms_per_sweep is not NULL, its time per sweep.  device_buf must be NULL.
- * Results are cached for the process by (device, shape, beta, steps, flags,
- * fixed options): a repeated call returns at once.  Scratch lattices are
+ * Results are cached for the process by (GPU name and multiprocessor count,
+ * shape, beta, steps, flags, fixed options): a repeated call returns at once.
+ * If the environment variable SUN_TUNE_CACHE names a file, results are also
+ * read from it (first call) and appended to it, one line per result.  Scratch lattices are
  * created one at a time (sun_footprint_bytes each).  Syncs; takes about 30 ms
  * of sweeps per candidate, 6 to 12 candidates. */
 sun_status sun_autotune(int nc, const int dims[4], double beta, int n_heatbath, int n_overrelax, int flags,

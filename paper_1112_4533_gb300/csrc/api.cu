@@ -625,6 +625,23 @@ sun_status sun_import_links(sun_lattice* L, const double* host, size_t n) {
   return SUN_OK;
 }
 
+sun_status sun_check_links(sun_lattice* L, double* max_unitarity_dev, double* max_det_dev, uint64_t* nonfinite) {
+  if (!L || !max_unitarity_dev || !max_det_dev || !nonfinite) return fail(SUN_ERR_ARG, "NULL argument");
+  SUN_TRY(set_device(L));
+  // results[4..6] hold the kernel's three words
+  unsigned long long* out = reinterpret_cast<unsigned long long*>(L->results + 4);
+  SUN_TRY(check_launch(L->ops->check_links(ctx_on(L, L->stream), out), "link check"));
+  SUN_CUDA(cudaMemcpyAsync(L->host_results + 4, out, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                           L->stream));
+  SUN_CUDA(cudaStreamSynchronize(L->stream));
+  unsigned long long w[3];
+  std::memcpy(w, L->host_results + 4, sizeof(w));
+  std::memcpy(max_unitarity_dev, &w[0], sizeof(double));
+  std::memcpy(max_det_dev, &w[1], sizeof(double));
+  *nonfinite = w[2];
+  return SUN_OK;
+}
+
 // The compact host format (stored rows in the storage precision): 4V x link_bytes.
 static sun_status copy_stored(sun_lattice* L, void* host, size_t bytes, bool to_host) {
   if (!L || !host) return fail(SUN_ERR_ARG, "NULL argument");

@@ -13,6 +13,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -30,13 +31,52 @@ struct Spec {
   double beta;
 };
 
+// the tuned fields of sun_options, and the winner's time per sweep
 struct Tuned {
-  sun_options opt;
+  int storage, block_threads, variant, reunit_mode;
   double ms;
 };
 
 std::mutex g_cache_mutex;
 std::map<std::string, Tuned> g_cache;
+bool g_file_loaded = false;
+
+// Optional persistent cache: the file named by SUN_TUNE_CACHE holds one line per
+// result, "key<TAB>storage block_threads variant reunit_mode ms"; it is read on
+// the first lookup and every new result is appended.  Keys include the GPU's name
+// and multiprocessor count, so one file can serve several kinds of GPU.
+const char* cache_file() {
+  const char* f = getenv("SUN_TUNE_CACHE");
+  return (f && *f) ? f : nullptr;
+}
+
+void load_cache_file() {  // with g_cache_mutex held
+  if (g_file_loaded) return;
+  g_file_loaded = true;
+  const char* path = cache_file();
+  if (!path) return;
+  FILE* f = fopen(path, "r");
+  if (!f) return;
+  char line[2048];
+  while (fgets(line, sizeof(line), f)) {
+    char* tab = strchr(line, '\t');
+    if (!tab) continue;
+    *tab = '\0';
+    Tuned t;
+    if (sscanf(tab + 1, "%d %d %d %d %lf", &t.storage, &t.block_threads, &t.variant, &t.reunit_mode, &t.ms) == 5)
+      g_cache[line] = t;
+  }
+  fclose(f);
+}
+
+void append_cache_file(const std::string& key, const Tuned& t) {  // with g_cache_mutex held
+  const char* path = cache_file();
+  if (!path) return;
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "%s\t%d %d %d %d %.6f\n", key.c_str(), t.storage, t.block_threads, t.variant, t.reunit_mode, t.ms);
+  fclose(f);
+}
 
 sun_status tune_fail(sun_status s, const char* msg) {
   sun::set_last_error_message(msg);
@@ -46,9 +86,16 @@ sun_status tune_fail(sun_status s, const char* msg) {
 std::string cache_key(const std::vector<Spec>& specs, int n_hb, int n_or, int flags, const sun_options& base,
                       int device) {
   std::string k;
-  char buf[256];
-  snprintf(buf, sizeof(buf), "%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|", device, n_hb, n_or, flags, base.precision,
-           base.reunit_every, base.use_graphs, (flags & SUN_TUNE_STORAGE) ? -1 : base.storage,
+  char buf[512];
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+    cudaGetLastError();
+    std::memset(&prop, 0, sizeof(prop));
+  }
+  for (char* c = prop.name; *c; ++c)
+    if (*c == '\t' || *c == '\n' || *c == '|') *c = '_';
+  snprintf(buf, sizeof(buf), "%s/%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|", prop.name, prop.multiProcessorCount, n_hb, n_or,
+           flags, base.precision, base.reunit_every, base.use_graphs, (flags & SUN_TUNE_STORAGE) ? -1 : base.storage,
            (flags & SUN_TUNE_REUNIT_MODE) ? -1 : base.reunit_mode, base.wave_lag);
   k += buf;
   for (const Spec& s : specs) {
@@ -156,12 +203,16 @@ sun_status autotune(const std::vector<Spec>& specs, int n_hb, int n_or, int flag
   const std::string key = cache_key(specs, n_hb, n_or, flags, *opt, device);
   {
     std::lock_guard<std::mutex> lock(g_cache_mutex);
+    load_cache_file();
     auto it = g_cache.find(key);
     if (it != g_cache.end()) {
-      sun_options o = it->second.opt;
-      o.stream = opt->stream;
-      *opt = o;
-      if (ms_out) *ms_out = it->second.ms;
+      const Tuned& t = it->second;
+      opt->storage = t.storage;
+      opt->block_threads = t.block_threads;
+      opt->variant = t.variant;
+      opt->reunit_mode = t.reunit_mode;
+      opt->wave_skip_units = 0;
+      if (ms_out) *ms_out = t.ms;
       return SUN_OK;
     }
   }
@@ -246,7 +297,9 @@ sun_status autotune(const std::vector<Spec>& specs, int n_hb, int n_or, int flag
 
   {
     std::lock_guard<std::mutex> lock(g_cache_mutex);
-    g_cache[key] = Tuned{best, best_ms};
+    const Tuned t{best.storage, best.block_threads, best.variant, best.reunit_mode, best_ms};
+    g_cache[key] = t;
+    append_cache_file(key, t);
   }
   best.stream = opt->stream;
   *opt = best;

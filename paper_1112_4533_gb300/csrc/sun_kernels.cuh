@@ -1388,6 +1388,58 @@ __global__ void __launch_bounds__(256) polyakov_kernel(const ObsParams p, const 
 }
 
 // ---------------------------------------------------------------------------
+// Health of the stored links: per link the largest entry of |U U^+ - 1| and
+// |det U - 1| in FP64 (of the stored values, the rebuilt row included), and
+// whether any entry is not finite.  out[0], out[1]: the maxima as the bit
+// patterns of non-negative doubles (ordered like the values, so an integer
+// atomicMax takes the maximum); out[2]: the count of non-finite links.
+// ---------------------------------------------------------------------------
+template <class R, int N, int S>
+__global__ void __launch_bounds__(256) check_links_kernel(const ObsParams p, unsigned long long* out) {
+  double dev = 0.0, ddet = 0.0;
+  unsigned long long bad = 0;
+  for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < 8 * p.g.Vh;
+       idx += int64_t(gridDim.x) * blockDim.x) {
+    const int b = int(idx / p.g.Vh);
+    const int64_t h = idx - int64_t(b) * p.g.Vh;
+    const Mat<double, N> m = mat_cast<R, double, N>(load_mat<R, N, S>(p.links + b * p.block_bytes, p.g.Vh, h));
+    bool finite = true;
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+#pragma unroll
+      for (int j = 0; j < N; ++j) finite = finite && isfinite(m.e[i][j].re) && isfinite(m.e[i][j].im);
+    if (!finite) {
+      ++bad;
+      continue;
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        // (U U^+)_ij = sum_k U_ik conj(U_jk)
+        Cpx<double> x = {0.0, 0.0};
+#pragma unroll
+        for (int k = 0; k < N; ++k) cfmac(x, m.e[i][k], m.e[j][k]);
+        if (i == j) x.re -= 1.0;
+        dev = fmax(dev, sqrt(x.re * x.re + x.im * x.im));
+      }
+    const Cpx<double> d = det_lu<N>(m);
+    ddet = fmax(ddet, sqrt((d.re - 1.0) * (d.re - 1.0) + d.im * d.im));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    dev = fmax(dev, __shfl_down_sync(0xffffffffu, dev, o));
+    ddet = fmax(ddet, __shfl_down_sync(0xffffffffu, ddet, o));
+    bad += __shfl_down_sync(0xffffffffu, bad, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(out, static_cast<unsigned long long>(__double_as_longlong(dev)));
+    atomicMax(out + 1, static_cast<unsigned long long>(__double_as_longlong(ddet)));
+    if (bad) atomicAdd(out + 2, bad);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Polyakov loop of a lattice cut into t-slabs: each slab multiplies U_t over its
 // interior slices, in t order, at every spatial site; then the slabs' partial
 // products are multiplied in slab order and traced (storage precision products,
@@ -2118,6 +2170,14 @@ cudaError_t launch_polyakov_combine(const Ctx& c, const void* const* parts, int 
 }
 
 template <class R, int N, int S>
+cudaError_t launch_check_links(const Ctx& c, unsigned long long* out) {
+  cudaError_t e = cudaMemsetAsync(out, 0, 3 * sizeof(unsigned long long), c.stream);
+  if (e != cudaSuccess) return e;
+  check_links_kernel<R, N, S><<<reduce_grid(c, 8 * c.g.Vh, 256), 256, 0, c.stream>>>(make_obs_params(c), out);
+  return cudaGetLastError();
+}
+
+template <class R, int N, int S>
 cudaError_t launch_export(const Ctx& c, double* dst, int64_t first, int64_t count) {
   if (count <= 0) return cudaSuccess;
   constexpr int LPB = conv_links_per_block<N>();
@@ -2246,6 +2306,7 @@ const Ops* ops_instance() {
       &launch_polyakov_partial<R, N, S>,
       &launch_polyakov_combine<R, N, S>,
       sizeof(PolyPart<R, N, S>),
+      &launch_check_links<R, N, S>,
       &launch_export<R, N, S>,
       &launch_import<R, N, S>,
       &launch_export_stored<R, N, S>,

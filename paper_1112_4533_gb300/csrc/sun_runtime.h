@@ -132,6 +132,8 @@ struct Ops {
   cudaError_t (*polyakov_combine)(const Ctx&, const void* const* parts, int n, double* out, const uint32_t* slot,
                                   int cap);
   size_t polyakov_partial_bytes;  // per spatial site
+  // max |U U^+ - 1|, max |det U - 1| (as double bit patterns) and the non-finite count into out[0..2]
+  cudaError_t (*check_links)(const Ctx&, unsigned long long* out);
   cudaError_t (*export_links)(const Ctx&, double* dst, int64_t first, int64_t count);
   cudaError_t (*import_links)(const Ctx&, const double* src, int64_t first, int64_t count);
   // the compact host format: stored rows in the storage precision, canonical order

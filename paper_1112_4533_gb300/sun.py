@@ -80,6 +80,7 @@ SIGNATURES = [
     ("sun_batch_create", ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int, _P, ctypes.c_int]),
     ("sun_batch_run", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D]),
     ("sun_batch_destroy", None, [_P]),
+    ("sun_check_links", ctypes.c_int, [_P, _D, _D, ctypes.POINTER(ctypes.c_uint64)]),
     ("sun_export_stored", ctypes.c_int, [_P, _P, ctypes.c_size_t]),
     ("sun_import_stored", ctypes.c_int, [_P, _P, ctypes.c_size_t]),
     ("sun_save_config", ctypes.c_int, [_P, ctypes.c_char_p]),
@@ -342,6 +343,13 @@ class Lattice:
     @heatbath_step.setter
     def heatbath_step(self, step):
         _check(self._lib.sun_set_heatbath_step(self.handle, int(step)))
+
+    def check_links(self):
+        """(max |U U^+ - 1|, max |det U - 1|, non-finite link count) over all links (sun_check_links)."""
+        dev, det = ctypes.c_double(), ctypes.c_double()
+        bad = ctypes.c_uint64()
+        _check(self._lib.sun_check_links(self.handle, ctypes.byref(dev), ctypes.byref(det), ctypes.byref(bad)))
+        return dev.value, det.value, int(bad.value)
 
     def export_stored(self, out=None):
         """The compact host format (sun_export_stored): a uint8 array of links_bytes."""

@@ -83,3 +83,26 @@ def test_autotuned_batch_keeps_chains_exact(sunlib):
         assert np.array_equal(L.export_links(), alone[i][0])
         assert np.abs(plaq[:, i] - alone[i][1]).max() < 1e-12
         L.close()
+
+
+def test_autotune_cache_file_persists_across_processes(tmp_path):
+    """SUN_TUNE_CACHE: a second process finds the first one's result in the file."""
+    import os
+    import subprocess
+    import sys
+    path = tmp_path / "tune.txt"
+    code = ("import time, paper_1112_4533_gb300 as p; t0 = time.perf_counter(); "
+            "r = p.autotune(3, (6, 6, 6, 6), 6.0, 1, 1); print(r['variant'], r['block_threads'], r['storage'], "
+            "time.perf_counter() - t0)")
+    env = dict(os.environ, SUN_TUNE_CACHE=str(path))
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    first = subprocess.run([sys.executable, "-c", code], env=env, cwd=root, capture_output=True, text=True, timeout=300)
+    assert first.returncode == 0, first.stderr
+    lines = path.read_text().splitlines()
+    assert len(lines) == 1 and "\t" in lines[0]
+    second = subprocess.run([sys.executable, "-c", code], env=env, cwd=root, capture_output=True, text=True, timeout=300)
+    assert second.returncode == 0, second.stderr
+    a, b = first.stdout.split(), second.stdout.split()
+    assert a[:3] == b[:3]
+    assert float(b[3]) < 0.05  # served from the file
+    assert len(path.read_text().splitlines()) == 1
