@@ -60,8 +60,13 @@ def updates_per_sweep():
 
 
 def source_digest():
+    """Digest of what defines the SU(3) update kernels' code: the device headers, the
+    SU(3) instantiation units and the compiler flags (host-only sources excluded)."""
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1112_4533_gb300", "csrc", "*"))):
+    pkg = os.path.join(ROOT, "paper_1112_4533_gb300")
+    files = [os.path.join(pkg, "csrc", n) for n in ("sun_device.cuh", "sun_kernels.cuh", "sun_runtime.h")]
+    files += sorted(glob.glob(os.path.join(pkg, "csrc", "ops_su3*.cu"))) + [os.path.join(pkg, "build.py")]
+    for p in files:
         with open(p, "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
