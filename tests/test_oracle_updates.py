@@ -57,6 +57,33 @@ def test_su2_overrelaxation_is_an_involution():
         assert np.abs(U1 - (S / k) @ dag(U) @ (S / k)).max() < 1e-13
 
 
+def test_su2_overrelaxation_is_gauge_covariant():
+    """For Nc = 2, W = U Sigma^+ goes to G(x) W G(x)^+ under a gauge transform,
+    so its normalised projection and (vhat^+)^2 do too, and the overrelaxed
+    link of the transformed field is the transform of the overrelaxed link:
+    OR(U^G) = OR(U)^G exactly, up to rounding, for every pass.  (The heatbath
+    is covariant only in distribution: its draw b is taken in a fixed frame.)"""
+    from tests.inputs import random_site_field
+    dims = (4, 4, 2, 6)
+    U = random_gauge_config(2, dims, seed=77)
+    G = random_site_field(2, dims, seed=78)
+
+    def transform(V):
+        out = np.empty_like(V)
+        for mu in range(4):
+            Gp = np.roll(G, -1, axis=3 - mu)  # x+mu: axes of G are (t, z, y, x)
+            out[mu] = G @ V[mu] @ dag(Gp)
+        return out
+
+    A, B = U.copy(), transform(U)
+    assert np.abs(B - U).max() > 0.1
+    for mu in range(4):
+        for par in (0, 1):
+            orc.update_pass(A, 2.3, orc.OVERRELAX, mu, par, 0, 5)
+            orc.update_pass(B, 2.3, orc.OVERRELAX, mu, par, 0, 5)
+    assert np.abs(transform(A) - B).max() < 1e-12
+
+
 @pytest.mark.parametrize("nc", [3, 4])
 def test_sun_overrelaxation_keeps_retr_u_sigma(nc):
     rng = np.random.default_rng(8 + nc)
