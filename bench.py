@@ -374,8 +374,9 @@ def gpu_arm(args):
                              reunit_mode=args.reunit_mode, tune_storage=True, tune_reunit_mode=True)
         tuned["tuning_s"] = time.perf_counter() - t0
         args.storage, args.variant, args.reunit_mode = tuned["storage"], tuned["variant"], tuned["reunit_mode"]
-        args.block = tuned["block_threads"]
-    kw = dict(precision=32, reunit_mode=args.reunit_mode, variant=args.variant, block_threads=args.block)
+        args.block, args.graph_sweeps = tuned["block_threads"], tuned["graph_sweeps"]
+    kw = dict(precision=32, reunit_mode=args.reunit_mode, variant=args.variant, block_threads=args.block,
+              graph_sweeps=args.graph_sweeps)
     L = sun.Lattice(NC, DIMS, BETA, hot_start=False, seed=1 + rank, storage=args.storage, **kw)
     L.run(W, N_HB, N_OR)
     barrier(world)
@@ -528,9 +529,9 @@ def batched_arm(args):
                                    tune_reunit_mode=True)
         tuned["tuning_s"] = time.perf_counter() - t0
         args.storage, args.variant, args.reunit_mode = tuned["storage"], tuned["variant"], tuned["reunit_mode"]
-        args.block = tuned["block_threads"]
+        args.block, args.graph_sweeps = tuned["block_threads"], tuned["graph_sweeps"]
     kw = dict(precision=32, storage=args.storage, reunit_mode=args.reunit_mode, variant=args.variant,
-              block_threads=args.block)
+              block_threads=args.block, graph_sweeps=args.graph_sweeps)
     lats = [sun.Lattice(3, (int(L),) * 4, float(b), hot_start=True, seed=100 + i, **kw)
             for i, (L, b) in enumerate(zip(Ls, betas))]
     updates = sum((1 + 4) * 4 * int(L) ** 4 for L in Ls) * sweeps
@@ -648,6 +649,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="fixed configuration from the flags, no autotuning")
     ap.add_argument("--block", type=int, default=0, help="threads per block of the update kernels (0 = 128)")
+    ap.add_argument("--graph-sweeps", type=int, default=0, help="sweeps captured per CUDA graph (0 = 1)")
     ap.add_argument("--workload", choices=["single", "batched", "serving"], default="single")
     ap.add_argument("--requests", type=int, default=80)
     ap.add_argument("--budget-gb", type=float, default=64.0)

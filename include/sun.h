@@ -107,6 +107,10 @@ enum { SUN_HEATBATH = 0, SUN_OVERRELAX = 1 };
  *  wave_lag      with variant bit 8: t-slices the even units run ahead of the odd
  *                ones (0 = default 3; clamped to [1, Nt-1]); results do not
  *                depend on it.
+ *  graph_sweeps  sweeps captured in one CUDA graph (sweeps per graph launch) by
+ *                sun_run and by a batch built from this lattice first; 0 = 1,
+ *                at most 64.  Results do not depend on it.  (With reunit_every
+ *                > 1 sun_run launches one sweep at a time.)
  *  wave_skip_units  fault injection for tests of the bounded waits, 0 in normal
  *                use: every wavefront launch leaves out its first k units (even
  *                links of slice 0 first), so the odd units that need them wait
@@ -126,6 +130,7 @@ typedef struct {
   int reunit_mode;
   int wave_lag;
   int wave_skip_units;
+  int graph_sweeps;
 } sun_options;
 
 int sun_abi_version(void);
@@ -339,7 +344,8 @@ sun_status sun_slabs_import_links(sun_slabs* slabs, const double* host, size_t n
  *   2. with SUN_TUNE_STORAGE: storage (Nc = 2: 4 or 8 reals, Nc = 3: 12 or 18)
  *   3. with SUN_TUNE_REUNIT_MODE: reunit_mode 0, 1, 2
  *   4. variant bit 8 (wavefront launches), for kernels that have that form
- * Bits 1, 4 and 8, block_threads and wave_lag leave the results bitwise
+ *   5. graph_sweeps 1, 4, 16 (sweeps per graph launch), with use_graphs
+ * Bits 1, 4, 8 and 16, block_threads, wave_lag and graph_sweeps leave the results bitwise
  * unchanged; storage, reunit_mode and bit 2 change them at the level of FP32
  * rounding (results stay within the FP32 tolerance of the FP64 oracle).
  */
@@ -353,7 +359,7 @@ enum {
  * n_heatbath + n_overrelax steps per sweep.  *opt supplies precision,
  * reunit_every, use_graphs, stream, wave_lag, and storage / reunit_mode where
  * those are not tuned; on success the fastest configuration is written back
- * into *opt (block_threads, variant, and the tuned fields) and, if
+ * into *opt (block_threads, variant, graph_sweeps and the tuned fields) and, if
  * ms_per_sweep is not NULL, its time per sweep.  device_buf must be NULL.
  * Results are cached for the process by (GPU name and multiprocessor count,
  * shape, beta, steps, flags, fixed options): a repeated call returns at once.

@@ -120,8 +120,10 @@ __global__ void bump_kernel(sun::DevState* st, uint32_t hb_steps, uint32_t slots
 
 struct GraphKey {
   int n_hb, n_or, reunit, plaq, poly;
+  int sweeps = 1;  // sweeps captured in the graph
   bool operator<(const GraphKey& o) const {
-    return std::tie(n_hb, n_or, reunit, plaq, poly) < std::tie(o.n_hb, o.n_or, o.reunit, o.plaq, o.poly);
+    return std::tie(n_hb, n_or, reunit, plaq, poly, sweeps) <
+           std::tie(o.n_hb, o.n_or, o.reunit, o.plaq, o.poly, o.sweeps);
   }
 };
 
@@ -136,7 +138,7 @@ struct sun_lattice {
   int dims[4] = {0, 0, 0, 0};
   double beta = 0.0;
   uint64_t seed = 0;
-  int reunit_every = 1, reunit_mode = 0, block_threads = 128, use_graphs = 1;
+  int reunit_every = 1, reunit_mode = 0, block_threads = 128, use_graphs = 1, graph_sweeps = 1;
   int device = 0;
   uint64_t sweeps_done = 0;
   cudaStream_t stream = nullptr;
@@ -236,8 +238,9 @@ sun_status get_graph(sun_lattice* L, const GraphKey& key, cudaGraphExec_t* out) 
     return SUN_OK;
   }
   SUN_CUDA(cudaStreamBeginCapture(L->capture_stream, cudaStreamCaptureModeThreadLocal));
-  sun_status st = enqueue_sweep(L, L->capture_stream, key.n_hb, key.n_or, key.reunit != 0, key.plaq != 0,
-                                key.poly != 0, true);
+  sun_status st = SUN_OK;
+  for (int k = 0; k < key.sweeps && st == SUN_OK; ++k)
+    st = enqueue_sweep(L, L->capture_stream, key.n_hb, key.n_or, key.reunit != 0, key.plaq != 0, key.poly != 0, true);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(L->capture_stream, &g);
   if (st != SUN_OK) {
@@ -290,6 +293,7 @@ void sun_options_init(sun_options* opt) {
   opt->device_buf = nullptr;
   opt->device_buf_bytes = 0;
   opt->use_graphs = 1;
+  opt->graph_sweeps = 0;
   opt->variant = 0;
   opt->reunit_mode = 0;
   opt->wave_lag = 0;
@@ -327,6 +331,8 @@ static sun_status resolve(int nc, const int* dims, const sun_options* opt_in, su
   if (opt->wave_lag < 0) return fail(SUN_ERR_ARG, "wave_lag = %d must be >= 0", opt->wave_lag);
   if (opt->wave_lag == 0) opt->wave_lag = kDefaultWaveLag;
   if (opt->wave_skip_units < 0) return fail(SUN_ERR_ARG, "wave_skip_units must be >= 0");
+  if (opt->graph_sweeps < 0 || opt->graph_sweeps > 64) return fail(SUN_ERR_ARG, "graph_sweeps must be in 0..64");
+  if (opt->graph_sweeps == 0) opt->graph_sweeps = 1;
   if (opt->reunit_mode < 0 || opt->reunit_mode > 2)
     return fail(SUN_ERR_ARG, "reunit_mode = %d must be 0, 1 or 2", opt->reunit_mode);
   if (opt->block_threads < 32 || opt->block_threads > 256 || (opt->block_threads & 31))
@@ -378,6 +384,7 @@ static sun_status create_lattice(sun_lattice** out, int nc, const int dims[4], d
   L->reunit_mode = opt.reunit_mode;
   L->block_threads = opt.block_threads;
   L->use_graphs = opt.use_graphs;
+  L->graph_sweeps = opt.graph_sweeps;
   L->ops = ops;
   L->plan = make_plan(nc, dims, ops->link_bytes);
 
@@ -521,16 +528,21 @@ sun_status sun_run(sun_lattice* L, int n_sweeps, int n_hb, int n_or, double* pla
   for (int done = 0; done < n_sweeps;) {
     const int chunk = (n_sweeps - done) < kHistCap ? (n_sweeps - done) : kHistCap;
     SUN_CUDA(cudaMemsetAsync(&L->ctx.state->slot, 0, sizeof(uint32_t), L->stream));
-    for (int k = 0; k < chunk; ++k) {
+    for (int k = 0; k < chunk;) {
       const bool reunit = reunit_due(L, L->sweeps_done);
+      // graph_sweeps sweeps per graph launch where every sweep re-unitarizes alike
+      const int per = (L->reunit_every <= 1 && chunk - k >= L->graph_sweeps) ? L->graph_sweeps : 1;
       if (L->use_graphs) {
         cudaGraphExec_t exec = nullptr;
-        SUN_TRY(get_graph(L, GraphKey{n_hb, n_or, reunit ? 1 : 0, plaq ? 1 : 0, poly ? 1 : 0}, &exec));
+        GraphKey key{n_hb, n_or, reunit ? 1 : 0, plaq ? 1 : 0, poly ? 1 : 0};
+        key.sweeps = per;
+        SUN_TRY(get_graph(L, key, &exec));
         SUN_CUDA(cudaGraphLaunch(exec, L->stream));
       } else {
-        SUN_TRY(enqueue_sweep(L, L->stream, n_hb, n_or, reunit, plaq, poly, true));
+        for (int q = 0; q < per; ++q) SUN_TRY(enqueue_sweep(L, L->stream, n_hb, n_or, reunit, plaq, poly, true));
       }
-      L->sweeps_done++;
+      L->sweeps_done += uint64_t(per);
+      k += per;
     }
     if (plaq)
       SUN_CUDA(cudaMemcpyAsync(plaq_hist + done, L->hist, chunk * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
@@ -935,6 +947,7 @@ struct sun_batch {
   int reunit_every = 1, reunit_mode = 0;
   uint64_t sweeps_done = 0;
   int use_graphs = 1;
+  int graph_sweeps = 1;  // sweeps per graph launch (from the first lattice's options)
   std::map<GraphKey, cudaGraphExec_t> graphs;
 };
 
@@ -1019,8 +1032,10 @@ sun_status get_batch_graph(sun_batch* B, const GraphKey& key, cudaGraphExec_t* o
     return SUN_OK;
   }
   SUN_CUDA(cudaStreamBeginCapture(B->capture_stream, cudaStreamCaptureModeThreadLocal));
-  sun_status st = enqueue_batch_sweep(B, B->capture_stream, key.n_hb, key.n_or, key.reunit != 0, key.plaq != 0,
-                                      key.poly != 0, true);
+  sun_status st = SUN_OK;
+  for (int k = 0; k < key.sweeps && st == SUN_OK; ++k)
+    st = enqueue_batch_sweep(B, B->capture_stream, key.n_hb, key.n_or, key.reunit != 0, key.plaq != 0, key.poly != 0,
+                             true);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(B->capture_stream, &g);
   if (st != SUN_OK) {
@@ -1070,6 +1085,7 @@ sun_status sun_batch_create(sun_batch** out, sun_lattice* const* lattices, int n
   B->reunit_every = L0->reunit_every;
   B->reunit_mode = L0->reunit_mode;
   B->use_graphs = use_graphs;
+  B->graph_sweeps = L0->graph_sweeps;
   if (cudaSetDevice(B->device) != cudaSuccess) return cleanup(fail(SUN_ERR_CUDA, "cudaSetDevice failed"));
   if (stream) {
     B->stream = static_cast<cudaStream_t>(stream);
@@ -1232,15 +1248,20 @@ sun_status sun_batch_run(sun_batch* B, int n_sweeps, int n_hb, int n_or, double*
   for (int done = 0; done < n_sweeps;) {
     const int chunk = std::min(n_sweeps - done, B->hist_cap);
     SUN_CUDA(cudaMemsetAsync(B->d_slot, 0, sizeof(uint32_t), B->stream));
-    for (int k = 0; k < chunk; ++k) {
+    for (int k = 0; k < chunk;) {
       const bool reunit = B->reunit_every == 1;
+      const int per = chunk - k >= B->graph_sweeps ? B->graph_sweeps : 1;
       if (B->use_graphs) {
         cudaGraphExec_t exec = nullptr;
-        SUN_TRY(get_batch_graph(B, GraphKey{n_hb, n_or, reunit ? 1 : 0, want_p ? 1 : 0, want_l ? 1 : 0}, &exec));
+        GraphKey key{n_hb, n_or, reunit ? 1 : 0, want_p ? 1 : 0, want_l ? 1 : 0};
+        key.sweeps = per;
+        SUN_TRY(get_batch_graph(B, key, &exec));
         SUN_CUDA(cudaGraphLaunch(exec, B->stream));
       } else {
-        SUN_TRY(enqueue_batch_sweep(B, B->stream, n_hb, n_or, reunit, want_p, want_l, true));
+        for (int q = 0; q < per; ++q)
+          SUN_TRY(enqueue_batch_sweep(B, B->stream, n_hb, n_or, reunit, want_p, want_l, true));
       }
+      k += per;
     }
     if (want_p || want_l) {
       SUN_CUDA(cudaMemcpyAsync(B->h_hist.data(), B->d_hist, size_t(3) * B->hist_cap * n * sizeof(double),

@@ -33,7 +33,7 @@ struct Spec {
 
 // the tuned fields of sun_options, and the winner's time per sweep
 struct Tuned {
-  int storage, block_threads, variant, reunit_mode;
+  int storage, block_threads, variant, reunit_mode, graph_sweeps;
   double ms;
 };
 
@@ -42,7 +42,7 @@ std::map<std::string, Tuned> g_cache;
 bool g_file_loaded = false;
 
 // Optional persistent cache: the file named by SUN_TUNE_CACHE holds one line per
-// result, "key<TAB>storage block_threads variant reunit_mode ms"; it is read on
+// result, "key<TAB>storage block_threads variant reunit_mode graph_sweeps ms"; it is read on
 // the first lookup and every new result is appended.  Keys include the GPU's name
 // and multiprocessor count, so one file can serve several kinds of GPU.
 const char* cache_file() {
@@ -63,7 +63,8 @@ void load_cache_file() {  // with g_cache_mutex held
     if (!tab) continue;
     *tab = '\0';
     Tuned t;
-    if (sscanf(tab + 1, "%d %d %d %d %lf", &t.storage, &t.block_threads, &t.variant, &t.reunit_mode, &t.ms) == 5)
+    if (sscanf(tab + 1, "%d %d %d %d %d %lf", &t.storage, &t.block_threads, &t.variant, &t.reunit_mode,
+               &t.graph_sweeps, &t.ms) == 6)
       g_cache[line] = t;
   }
   fclose(f);
@@ -74,7 +75,8 @@ void append_cache_file(const std::string& key, const Tuned& t) {  // with g_cach
   if (!path) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s\t%d %d %d %d %.6f\n", key.c_str(), t.storage, t.block_threads, t.variant, t.reunit_mode, t.ms);
+  fprintf(f, "%s\t%d %d %d %d %d %.6f\n", key.c_str(), t.storage, t.block_threads, t.variant, t.reunit_mode,
+          t.graph_sweeps, t.ms);
   fclose(f);
 }
 
@@ -211,6 +213,7 @@ sun_status autotune(const std::vector<Spec>& specs, int n_hb, int n_or, int flag
       opt->block_threads = t.block_threads;
       opt->variant = t.variant;
       opt->reunit_mode = t.reunit_mode;
+      opt->graph_sweeps = t.graph_sweeps;
       opt->wave_skip_units = 0;
       if (ms_out) *ms_out = t.ms;
       return SUN_OK;
@@ -223,6 +226,7 @@ sun_status autotune(const std::vector<Spec>& specs, int n_hb, int n_or, int flag
   best.variant = 0;
   best.block_threads = 128;
   best.wave_skip_units = 0;
+  best.graph_sweeps = 1;
   double best_ms = -1.0;
   const bool fp32 = best.precision == 32;
 
@@ -295,9 +299,20 @@ sun_status autotune(const std::vector<Spec>& specs, int n_hb, int n_or, int flag
           },
           best, best_ms);
 
+  // 5. sweeps per graph launch (amortises the launch of short sweeps)
+  if (best.use_graphs) {
+    const int per[2] = {4, 16};
+    stage(specs, n_hb, n_or, 2,
+          [&](int c, sun_options& o) {
+            o.graph_sweeps = per[c];
+            return true;
+          },
+          best, best_ms);
+  }
+
   {
     std::lock_guard<std::mutex> lock(g_cache_mutex);
-    const Tuned t{best.storage, best.block_threads, best.variant, best.reunit_mode, best_ms};
+    const Tuned t{best.storage, best.block_threads, best.variant, best.reunit_mode, best.graph_sweeps, best_ms};
     g_cache[key] = t;
     append_cache_file(key, t);
   }

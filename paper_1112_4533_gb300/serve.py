@@ -98,7 +98,7 @@ class Server:
     between its ticks, and leave as soon as they are done."""
 
     def __init__(self, hbm_budget, n_overrelax=4, sweeps_per_tick=None, precision=32, use_graphs=True,
-                 work_cap_ms=3.0, tick_ms=40.0, policy="srpt", clock=time.perf_counter):
+                 work_cap_ms=3.0, tick_ms=40.0, policy="srpt", graph_sweeps=16, clock=time.perf_counter):
         if policy not in ("srpt", "fifo"):
             raise ValueError("policy must be 'srpt' or 'fifo'")
         self.work_cap = work_cap_ms
@@ -109,6 +109,9 @@ class Server:
         self.policy = policy
         self.precision = precision
         self.use_graphs = use_graphs
+        # sweeps per graph launch: a tick of small chains runs up to hundreds of
+        # sweeps of a few microseconds each
+        self.graph_sweeps = int(graph_sweeps)
         self.clock = clock
         self.ticks = 0
         self.link_updates = 0
@@ -142,7 +145,8 @@ class Server:
             while pending and pending[0].arrival <= now and used + footprint(pending[0], self.precision) <= self.budget:
                 r = pending.pop(0)
                 fp = footprint(r, self.precision)
-                lat = sun.Lattice(r.nc, r.dims, r.beta, hot_start=True, seed=r.seed, precision=self.precision)
+                lat = sun.Lattice(r.nc, r.dims, r.beta, hot_start=True, seed=r.seed, precision=self.precision,
+                                  graph_sweeps=self.graph_sweeps)
                 r.t_admit = self.clock() - t0
                 active.append([r, lat, 0, [], [], fp])
                 used += fp

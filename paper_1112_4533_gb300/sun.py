@@ -31,7 +31,8 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("storage", ctypes.c_int), ("reunit_every", ctypes.c_int),
                 ("block_threads", ctypes.c_int), ("stream", ctypes.c_void_p), ("device_buf", ctypes.c_void_p),
                 ("device_buf_bytes", ctypes.c_size_t), ("use_graphs", ctypes.c_int), ("variant", ctypes.c_int),
-                ("reunit_mode", ctypes.c_int), ("wave_lag", ctypes.c_int), ("wave_skip_units", ctypes.c_int)]
+                ("reunit_mode", ctypes.c_int), ("wave_lag", ctypes.c_int), ("wave_skip_units", ctypes.c_int),
+                ("graph_sweeps", ctypes.c_int)]
 
 
 class LatticeInfo(ctypes.Structure):
@@ -133,7 +134,8 @@ def _dims(dims):
 
 
 def _options(precision=32, storage=0, reunit_every=1, block_threads=0, stream=None, device_buf=None,
-             device_buf_bytes=0, use_graphs=True, variant=0, reunit_mode=0, wave_lag=0, wave_skip_units=0):
+             device_buf_bytes=0, use_graphs=True, variant=0, reunit_mode=0, wave_lag=0, wave_skip_units=0,
+             graph_sweeps=0):
     o = Options()
     load_library().sun_options_init(ctypes.byref(o))
     o.precision = int(precision)
@@ -148,12 +150,13 @@ def _options(precision=32, storage=0, reunit_every=1, block_threads=0, stream=No
     o.reunit_mode = int(reunit_mode)
     o.wave_lag = int(wave_lag)
     o.wave_skip_units = int(wave_skip_units)
+    o.graph_sweeps = int(graph_sweeps)
     return o
 
 
 def _tuned(o, ms):
     return {"storage": o.storage, "block_threads": o.block_threads, "variant": o.variant,
-            "reunit_mode": o.reunit_mode, "ms_per_sweep": ms.value}
+            "reunit_mode": o.reunit_mode, "graph_sweeps": o.graph_sweeps, "ms_per_sweep": ms.value}
 
 
 def autotune(nc, dims, beta, n_heatbath=1, n_overrelax=4, precision=32, storage=0, reunit_mode=0,
@@ -216,7 +219,7 @@ class Lattice:
 
     def __init__(self, nc, dims, beta, hot_start=False, seed=1, precision=32, storage=0, reunit_every=1,
                  block_threads=0, stream=None, use_graphs=True, device=None, variant=0, reunit_mode=0,
-                 wave_lag=0, wave_skip_units=0):
+                 wave_lag=0, wave_skip_units=0, graph_sweeps=0):
         import torch  # device memory and streams only
 
         self.nc = int(nc)
@@ -238,7 +241,7 @@ class Lattice:
         aligned = (base + 255) // 256 * 256
         o = _options(precision, storage, reunit_every, block_threads, ctypes.c_void_p(self.stream.cuda_stream),
                      ctypes.c_void_p(aligned), nbytes, use_graphs, variant, reunit_mode, wave_lag,
-                     wave_skip_units)
+                     wave_skip_units, graph_sweeps)
         # the tensor's memory must be usable on our stream
         self.stream.wait_stream(torch.cuda.current_stream(dev))
         h = ctypes.c_void_p()

@@ -122,7 +122,7 @@ def test_autotune_rejects_invalid_requests_on_the_host(lib):
 def test_wavefront_options_validated_on_the_host(lib):
     from paper_1112_4533_gb300 import sun
     h = ctypes.c_void_p()
-    for field, bad in (("variant", 32), ("wave_lag", -1), ("wave_skip_units", -2)):
+    for field, bad in (("variant", 32), ("wave_lag", -1), ("wave_skip_units", -2), ("graph_sweeps", 65)):
         o = sun._options()
         setattr(o, field, bad)
         assert lib.sun_lattice_create(ctypes.byref(h), 3, _dims((4, 4, 4, 4)), 6.0, 0, 1, ctypes.byref(o)) == 1

@@ -26,7 +26,7 @@ def sunlib():
 
 
 def lattice_kwargs(t):
-    return {k: t[k] for k in ("storage", "block_threads", "variant", "reunit_mode")}
+    return {k: t[k] for k in ("storage", "block_threads", "variant", "reunit_mode", "graph_sweeps")}
 
 
 def test_autotune_su3_picks_a_valid_configuration(sunlib):
@@ -36,6 +36,7 @@ def test_autotune_su3_picks_a_valid_configuration(sunlib):
     assert t["block_threads"] in (64, 128, 256)
     assert t["variant"] & ~(1 | 8) == 0  # no two-row staple unless asked for
     assert t["reunit_mode"] in (0, 1, 2)
+    assert t["graph_sweeps"] in (1, 4, 16)
     assert t["ms_per_sweep"] > 0.0
     # the tuned lattice follows the oracle through one overrelaxation pass
     U0 = random_gauge_config(3, dims, 90)

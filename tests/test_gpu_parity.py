@@ -391,6 +391,29 @@ def test_graph_replay_equals_direct_launches(sunlib):
     assert np.array_equal(res[0][2], res[1][2])
 
 
+def test_multi_sweep_graphs_equal_one_sweep_graphs(sunlib):
+    """graph_sweeps: 4 sweeps per graph launch (then a remainder of single
+    sweeps) gives bitwise the links and histories of one sweep per launch."""
+    dims = (6, 4, 4, 6)
+    out = []
+    for gs in (1, 4):
+        with sunlib.Lattice(3, dims, 6.0, hot_start=True, seed=14, graph_sweeps=gs, reunit_mode=1) as L:
+            plaq, poly = L.run(6, 1, 2)
+            plaq2, _ = L.run(3, 1, 2)
+            out.append((plaq, poly, plaq2, L.export_links(), L.heatbath_step))
+    assert all(np.array_equal(a, b) for a, b in zip(out[0][:4], out[1][:4]))
+    assert out[0][4] == out[1][4] == 9
+    lats = [sunlib.Lattice(2, (4, 4, 4, 4), 2.3, hot_start=True, seed=15 + i, graph_sweeps=4) for i in range(3)]
+    with sunlib.Batch(lats) as B:
+        bp, _ = B.run(5, 1, 1)
+    for i, L in enumerate(lats):
+        with sunlib.Lattice(2, (4, 4, 4, 4), 2.3, hot_start=True, seed=15 + i) as A:
+            ap, _ = A.run(5, 1, 1)
+            assert np.array_equal(A.export_links(), L.export_links())
+        assert np.abs(bp[:, i] - ap).max() < 1e-12
+        L.close()
+
+
 def test_runs_are_deterministic(sunlib):
     out = []
     for _ in range(2):

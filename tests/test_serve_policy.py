@@ -24,7 +24,7 @@ def sim(monkeypatch):
     S = Sim()
 
     class FakeLattice:
-        def __init__(self, nc, dims, beta, hot_start=True, seed=1, precision=32):
+        def __init__(self, nc, dims, beta, hot_start=True, seed=1, precision=32, graph_sweeps=1):
             self.nc, self.dims, self.seed = nc, dims, seed
             S.resident += 1
 
