@@ -464,7 +464,10 @@ def gpu_arm(args):
         cpu = oracle_leg(L, 8 * NC * NC * V, args.cpu_seconds)
 
     L.close()
-    launches_per_sweep = (N_HB + N_OR) * 8 + 4  # passes, reunitarization, plaquette, Polyakov, counter
+    # kernels per sweep: the passes (8 per step, or 4 wavefront launches with bit 8), the separate
+    # re-unitarization (placement 0 only), plaquette, Polyakov loop, step counter
+    passes_per_step = 4 if (args.variant & 8) and not (args.variant & 18) else 8
+    launches_per_sweep = (N_HB + N_OR) * passes_per_step + (1 if args.reunit_mode == 0 else 0) + 3
     out = {
         "metric": METRIC,
         "value": value,
@@ -567,6 +570,9 @@ def batched_arm(args):
                       "link_updates_per_step": updates, "storage_reals": args.storage, "kernel_variant": args.variant,
                       "block_threads": args.block, "reunit_mode": args.reunit_mode, "autotuned": tuned},
            "link_updates_per_s": updates / tb,
+           # per batch sweep of the one SU(3) group: 40 passes, the separate re-unitarization
+           # (placement 0), plaquette and Polyakov partials and their per-chain sums, two counters
+           "gpu_launches": args.steps * sweeps * (40 + (1 if args.reunit_mode == 0 else 0) + 4 + 2),
            "plain": {"value": n / tpl, "unit": "chains/s", "ms_per_step": tpl * 1e3, "link_updates_per_s": updates / tpl,
                      "path": "each chain alone, sun_run of 50 sweeps (one captured sweep graph per chain)"},
            "speedup_vs_plain": tpl / tb}
