@@ -499,3 +499,35 @@ def test_invalid_pass_arguments_raise(sunlib):
                 L.update_pass(*args)
         with pytest.raises(sunlib.SunError):
             L.heatbath_step = 2 ** 33
+
+
+def test_lattices_on_concurrent_host_threads(sunlib):
+    """Two lattices driven at the same time from two host threads (the C ABI
+    releases the interpreter lock): each ends bitwise where it ends alone."""
+    import threading
+    specs = [(3, (8, 6, 4, 6), 6.0, 31), (2, (6, 6, 6, 8), 2.3, 32)]
+    alone = []
+    for nc, dims, beta, seed in specs:
+        with sunlib.Lattice(nc, dims, beta, hot_start=True, seed=seed) as L:
+            L.run(12, 1, 3)
+            alone.append(L.export_links())
+    out, errors = [None, None], []
+
+    def work(i):
+        try:
+            nc, dims, beta, seed = specs[i]
+            with sunlib.Lattice(nc, dims, beta, hot_start=True, seed=seed) as L:
+                for _ in range(3):
+                    L.run(4, 1, 3)
+                out[i] = L.export_links()
+        except Exception as e:  # reported below
+            errors.append(e)
+
+    threads = [threading.Thread(target=work, args=(i,)) for i in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    for got, want in zip(out, alone):
+        assert np.array_equal(got, want)
