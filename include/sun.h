@@ -75,8 +75,8 @@ enum { SUN_HEATBATH = 0, SUN_OVERRELAX = 1 };
  *  use_graphs    sun_run captures one sweep as a CUDA graph and replays it (default 1).
  *  variant       update-pass kernel variant, bit flags (default 0); results do not
  *                depend on bits 1 and 4:
- *                1 = (SU(3) FP32) bound the registers for 5 resident 128-thread
- *                blocks per SM;
+ *                1 = (SU(3), SU(4) FP32) bound the registers for 5 (SU(3)) or 4
+ *                (SU(4), per-link kernel) resident 128-thread blocks per SM;
  *                2 = (SU(3) FP32 two-row storage) multiply out rows 0 and 1 of each
  *                staple term only and take its third row as conj(row0 x row1),
  *                exact for SU(3) products (results move by the order of the
@@ -338,7 +338,8 @@ sun_status sun_slabs_import_links(sun_slabs* slabs, const double* host, size_t n
  * swept with each candidate configuration through sun_run / sun_batch_run and
  * the fastest is kept.  The search goes one option at a time, each stage
  * starting from the best of the previous one:
- *   1. kernel shape: block_threads 64, 128, 256; variant bit 1 (SU(3) FP32);
+ *   1. kernel shape: block_threads 64, 128, 256; variant bit 1 (SU(3) FP32, and
+ *      SU(4) FP32 for a single lattice);
  *      per-link or row-parallel kernel (bit 4, Nc 4 and 6); with
  *      SUN_TUNE_TWO_ROW also bit 2
  *   2. with SUN_TUNE_STORAGE: storage (Nc = 2: 4 or 8 reals, Nc = 3: 12 or 18)

@@ -230,7 +230,7 @@ sun_status autotune(const std::vector<Spec>& specs, int n_hb, int n_or, int flag
   double best_ms = -1.0;
   const bool fp32 = best.precision == 32;
 
-  // 1. kernel shape: block size, 6-blocks/SM register bound (SU(3) FP32),
+  // 1. kernel shape: block size, register bound (SU(3), SU(4) FP32),
   //    row-parallel vs per-link kernel (Nc 4, 6), two-row staple if allowed
   struct Shape {
     int variant, block;
@@ -255,6 +255,8 @@ sun_status autotune(const std::vector<Spec>& specs, int n_hb, int n_or, int flag
     const int per_link = nc0 == 6 ? 4 : 0;
     for (Shape& s : shapes) s.variant = per_link;
     shapes.push_back({row_parallel, 128});
+    // the register-bounded per-link pass (its own launches only: the batch kernels ignore it)
+    if (nc0 == 4 && fp32 && own_launches) shapes.push_back({1, 128});
   }
   stage(specs, n_hb, n_or, int(shapes.size()),
         [&](int c, sun_options& o) {

@@ -16,6 +16,12 @@ constexpr int kMaxBlockThreads = 256;
 // are compiled for: 5 measured fastest among 5..8 for the SU(3) FP32 passes on
 // GB300 (more warps cost more spills than they hide latency)
 constexpr int kOccBlocks = 5;
+// the same bound for the SU(4) FP32 per-link passes: 4 blocks (128 registers)
+constexpr int kOccBlocksSU4 = 4;
+template <int N>
+__host__ __device__ constexpr int occ_blocks() {
+  return N == 4 ? kOccBlocksSU4 : kOccBlocks;
+}
 constexpr int kHeatbathMode = 0;
 constexpr int kOverrelaxMode = 1;
 
@@ -416,7 +422,7 @@ __device__ __forceinline__ void pass_body(const PassParams& p, int par, int64_t 
   store_mat<R, N, S>(ublk, g.Vh, h, u);
 }
 
-// VAR bit 0: at most 128 threads per block and registers for kOccBlocks blocks per SM;
+// VAR bit 0: at most 128 threads per block and registers for occ_blocks<N>() blocks per SM;
 // VAR bit 1: two-row staple products (SU(3) two-row storage only).
 // REUNIT: the FP64 re-unitarization of selected links is compiled in (passes that
 // re-unitarize use this instantiation; the others carry no FP64 code).
@@ -428,7 +434,7 @@ __global__ void __launch_bounds__(kMaxBlockThreads) update_pass_mat(const PassPa
 }
 
 template <class R, int N, int S, int MODE, int VAR, bool REUNIT>
-__global__ void __launch_bounds__(128, kOccBlocks) update_pass_mat_occ(const PassParams p) {
+__global__ void __launch_bounds__(128, occ_blocks<N>()) update_pass_mat_occ(const PassParams p) {
   const int64_t h = p.h_begin + int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (h >= p.h_end) return;
   pass_body<R, N, S, MODE, (VAR & 2) != 0, REUNIT>(p, p.parity, h);
@@ -787,6 +793,12 @@ constexpr bool has_fused_reunit() {
 template <class R, int N, int S>
 constexpr bool has_variants() {
   return std::is_same<R, float>::value && N == 3;
+}
+
+// the register-bounded per-link pass (variant bit 1) is also built for SU(4) FP32
+template <class R, int N>
+constexpr bool has_occ_bound() {
+  return std::is_same<R, float>::value && N == 4;
 }
 
 // ---------------------------------------------------------------------------
@@ -1974,6 +1986,23 @@ cudaError_t launch_pass(const Ctx& c, int mode, int mu, int parity, uint32_t ste
     }
 #undef SUN_LAUNCH_VAR
   } else {
+    if constexpr (has_occ_bound<R, N>()) {
+      if (c.variant & 1) {
+        const unsigned g1 = unsigned((n_links + 127) / 128);
+        if (mode == kHeatbathMode) {
+          if (ru)
+            update_pass_mat_occ<R, N, S, kHeatbathMode, 1, true><<<g1, 128, 0, c.stream>>>(p);
+          else
+            update_pass_mat_occ<R, N, S, kHeatbathMode, 1, false><<<g1, 128, 0, c.stream>>>(p);
+        } else {
+          if (ru)
+            update_pass_mat_occ<R, N, S, kOverrelaxMode, 1, true><<<g1, 128, 0, c.stream>>>(p);
+          else
+            update_pass_mat_occ<R, N, S, kOverrelaxMode, 1, false><<<g1, 128, 0, c.stream>>>(p);
+        }
+        return cudaGetLastError();
+      }
+    }
     if (mode == kHeatbathMode) {
       if (ru)
         update_pass_mat<R, N, S, kHeatbathMode, 0, true><<<grid, bt, 0, c.stream>>>(p);

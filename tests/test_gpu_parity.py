@@ -531,3 +531,18 @@ def test_lattices_on_concurrent_host_threads(sunlib):
     assert not errors, errors
     for got, want in zip(out, alone):
         assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("reunit_mode", [0, 1, 2])
+def test_su4_register_bound_equals_default_kernel(sunlib, reunit_mode):
+    """SU(4) FP32 with variant bit 1 (the per-link pass bounded to 128 registers)
+    gives bitwise the links and observables of the default kernel."""
+    for dims in [(6, 6, 4, 8), (4, 4, 4, 4)]:
+        out = []
+        for variant in (0, 1):
+            with sunlib.Lattice(4, dims, 11.0, hot_start=True, seed=21, variant=variant,
+                                reunit_mode=reunit_mode) as L:
+                plaq, poly = L.run(2, 1, 2)
+                out.append((L.export_links(), plaq, poly))
+        assert np.array_equal(out[0][0], out[1][0]), dims
+        assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][2], out[1][2])
