@@ -27,7 +27,8 @@ def beta_for(nc):
 
 # (nc, storage, precision, variant, re-unitarization modes)
 CASES = [(2, 4, 32, 0, (0, 1, 2)), (2, 8, 64, 0, (0,)), (3, 12, 32, 1, (0, 1, 2)), (3, 18, 32, 16, (1,)),
-         (3, 12, 64, 0, (0,)), (3, 12, 32, 9, (1,)), (4, 32, 32, 0, (1,)), (6, 72, 32, 0, (0,))]
+         (3, 12, 64, 0, (0,)), (3, 12, 32, 9, (1,)), (4, 32, 32, 0, (1,)), (4, 32, 32, 1, (0, 2)),
+         (6, 72, 32, 0, (0,))]
 
 
 @pytest.mark.parametrize("nc,st,prec,var,modes", CASES)
