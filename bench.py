@@ -618,7 +618,7 @@ def reference_arm(args):
     if rank != 0:
         return
     K, W = args.steps, args.warmup
-    per = max(2.0, min(20.0, 150.0 / max(1, K + W)))
+    per = max(1.0, min(args.cpu_seconds, 150.0 / max(1, K + W)))
     for _ in range(W):
         oracle_sample(per / 4)
     rates, cores, desc = [], 1, ""
@@ -628,7 +628,7 @@ def reference_arm(args):
         rates.append(r)
     dt = time.perf_counter() - t0
     value = sum(rates) / len(rates)
-    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 0, "steps": K,
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus, "steps": K,
            "warmup": W, "ms_per_step": dt / K * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic (cold start)",
            "config": {"workload": WORKLOAD_NAME, "nc": NC, "dims": list(DIMS), "beta": BETA,
@@ -649,7 +649,8 @@ def main():
                     help="update-kernel variant bits: 1 = 5 blocks/SM register bound, 2 = two-row staple")
     ap.add_argument("--reunit-mode", type=int, default=1, choices=[0, 1, 2])
     ap.add_argument("--e2e-steps", type=int, default=8)
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="seconds of oracle work in the cpu_baseline leg, and the cap of one --impl reference step")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
