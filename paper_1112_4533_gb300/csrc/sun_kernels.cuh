@@ -1357,16 +1357,25 @@ __device__ __forceinline__ void site_polyakov(const ObsParams& p, int64_t xs, do
 }
 
 // <P> of one lattice: grid-stride over sites, deterministic FP64 reduction.
-// The whole lattice: sites idx < V in parity-block order.  (A loop over a
-// sub-range here costs SU(6) its register allocation: a kernel of its own does
-// the slabs.)
+// Nc <= 4: idx < V visits half-site idx / 2 of parity idx % 2, both parities
+// of a half-site in turn.  A link is read as its own site's link and as a
+// forward neighbour of the other parity at nearby half-site indices (within
+// Nx Ny Nz / 2), so the second read finds it in L2; in parity-block order the
+// two reads are half the lattice apart and each link comes from DRAM twice.
+// Nc >= 5 keeps parity-block order, whose loop keeps SU(6) FP32 from spilling
+// (its plaquette is arithmetic-bound).  (A loop over a sub-range here costs
+// SU(6) its register allocation too: a kernel of its own does the slabs.)
 template <class R, int N, int S>
 __global__ void __launch_bounds__(256) plaquette_kernel(const ObsParams p, const ReduceParams rp) {
   double acc[1] = {0.0};
   for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < p.g.V;
        idx += int64_t(gridDim.x) * blockDim.x) {
-    const int par = idx >= p.g.Vh ? 1 : 0;
-    acc[0] += site_plaquette<R, N, S>(p, par, idx - par * p.g.Vh);
+    if constexpr (N <= 4) {
+      acc[0] += site_plaquette<R, N, S>(p, int(idx & 1), idx >> 1);
+    } else {
+      const int par = idx >= p.g.Vh ? 1 : 0;
+      acc[0] += site_plaquette<R, N, S>(p, par, idx - par * p.g.Vh);
+    }
   }
   reduce_finish<1>(acc, rp);
 }
