@@ -3,7 +3,6 @@ configuration the library accepts, the configuration it picks keeps the
 update within the FP32 tolerance of the oracle, repeated calls come from the
 cache, and a batch built with the tuned options still evolves every chain
 exactly as alone."""
-import time
 
 import numpy as np
 import pytest
@@ -52,9 +51,8 @@ def test_autotune_su3_picks_a_valid_configuration(sunlib):
 def test_autotune_is_cached(sunlib):
     dims = (6, 6, 6, 6)
     a = sunlib.autotune(2, dims, 2.3, 1, 1)
-    t0 = time.perf_counter()
     b = sunlib.autotune(2, dims, 2.3, 1, 1)
-    assert time.perf_counter() - t0 < 0.05
+    # ms_per_sweep included: a new measurement would not repeat the first one's time
     assert a == b
 
 
