@@ -55,6 +55,15 @@ def volume(d):
     return d[0] * d[1] * d[2] * d[3]
 
 
+def workload_config(world):
+    """The workload both arms (this one and --impl reference) are measured on."""
+    return {"workload": WORKLOAD_NAME, "nc": NC, "dims": list(DIMS), "beta": BETA, "start": "cold",
+            "n_heatbath": N_HB, "n_overrelax": N_OR, "link_updates_per_step": updates_per_sweep(),
+            "reunitarize": "FP64, every link once per sweep",
+            "observables": "FP64 plaquette + Polyakov every sweep",
+            "l2": "lattice (2.0 GB two-row FP32) larger than L2, no flush", "parallelism": f"replicas x{world}"}
+
+
 def updates_per_sweep():
     return (N_HB + N_OR) * 4 * volume(DIMS)
 
@@ -199,13 +208,33 @@ def oracle_sample(target_seconds=12.0, threads=None, max_slices=24):
     return r, cores, desc
 
 
+def oracle_input(threads=None):
+    """The 48^3 x 96 configuration the oracle leg starts from, made by the oracle
+    alone: a 16^3 x 32 lattice thermalised from a cold start (six sweeps of
+    1 heatbath + 4 overrelaxation at beta 6.2), tiled 3 x 3 x 3 x 3 (a periodic
+    configuration of the large lattice whose neighbourhoods are the small
+    one's).  Returned in canonical order, complex128."""
+    import numpy as np
+    import oracle as orc
+
+    orc.set_threads(threads or os.cpu_count() or 1)
+    tile = (16, 16, 16, 32)
+    U = orc.init(NC, tile, False, 13)
+    for s in range(6):
+        orc.sweep(U, BETA, 1, 4, True, 13, s)
+    reps = tuple(d // t for d, t in zip(DIMS, tile))
+    return np.tile(U, (1, reps[3], reps[2], reps[1], reps[0], 1, 1))
+
+
 def oracle_leg(L, n_doubles, target_seconds=12.0, max_slices=24):
-    """The CPU baseline on the GPU's own configuration, with the agreement of
-    the two stated: the FP64 oracle measures the plaquette and Polyakov loop of
-    the configuration the GPU holds after the timed sweeps, then repeats one
-    heatbath pass and one overrelaxation pass of the GPU (same input, same
-    Philox counters) on the first time slices, timing each (rates combined 1:5
-    as in a sweep).  Returns the cpu_baseline dict with an "agreement" entry."""
+    """The CPU baseline with the agreement of the two stated.  The oracle makes
+    its own thermalised 48^3 x 96 configuration (oracle_input); the GPU lattice
+    is loaded with it (after the timed sweeps), and both measure its plaquette
+    and Polyakov loop.  Then one heatbath pass and one overrelaxation pass:
+    the GPU on the whole lattice, the oracle on the first time slices (same
+    input, same Philox counters), each oracle pass timed (rates combined 1:5
+    as in a sweep); the second pass starts from the oracle's result of the
+    first.  Returns the cpu_baseline dict with an "agreement" entry."""
     import numpy as np
     import torch
     import oracle as orc
@@ -214,27 +243,31 @@ def oracle_leg(L, n_doubles, target_seconds=12.0, max_slices=24):
     cores = orc.set_threads(os.cpu_count() or 1)
     nx, ny, nz, nt = DIMS
     shape = (4, nt, nz, ny, nx, NC, NC)
+    t0 = time.perf_counter()
+    U = oracle_input()
+    t_input = time.perf_counter() - t0
     a = torch.empty(n_doubles, dtype=torch.float64).pin_memory()
     b = torch.empty(n_doubles, dtype=torch.float64).pin_memory()
     A = a.numpy().view(np.complex128).reshape(shape)
     B = b.numpy().view(np.complex128).reshape(shape)
-    L.export_links_raw(a.data_ptr(), n_doubles)
+    A[...] = U
+    del U
+    L.import_links_raw(a.data_ptr(), n_doubles)
     p_gpu = L.plaquette()
     l_gpu = L.polyakov_loop()
     t0 = time.perf_counter()
     p_orc = orc.plaquette(A)
     t_plaq = time.perf_counter() - t0
-    l_orc = orc.polyakov(A)
-    l_orc = complex(l_orc[0], l_orc[1]) if isinstance(l_orc, tuple) else complex(l_orc)
-    step = L.heatbath_step
+    l_orc = complex(orc.polyakov(A))
+    step = 7
+    L.heatbath_step = step
     n_slab = max(1, min(max_slices, nt - 2))
     per_pass = nx * ny * nz // 2 * n_slab
 
     def slab_diff(X, Y):
-        d = np.abs(X[:, :n_slab] - Y[:, :n_slab]).reshape(4, n_slab, -1, NC * NC).max(axis=-1)
-        return d
+        return np.abs(X[:, :n_slab] - Y[:, :n_slab]).reshape(4, n_slab, -1, NC * NC).max(axis=-1)
 
-    # heatbath pass (mu 1, even) from A: GPU on the whole lattice, oracle on the slab
+    # heatbath pass (mu 1, even): GPU on the whole lattice, oracle on the slab
     L.update_pass(sun.HEATBATH, 1, 0)
     L.export_links_raw(b.data_ptr(), n_doubles)
     n_hb, t_hb = 0, 0.0
@@ -245,11 +278,12 @@ def oracle_leg(L, n_doubles, target_seconds=12.0, max_slices=24):
     d = slab_diff(A, B)
     flips = int((d > 1e-5).sum())
     hb_err = float(d[d <= 1e-5].max())
-    # overrelaxation pass (mu 2, odd) from the GPU's post-heatbath state B
+    # overrelaxation pass (mu 2, odd), both from the oracle's post-heatbath links
+    L.import_links_raw(a.data_ptr(), n_doubles)
     L.update_pass(sun.OVERRELAX, 2, 1)
-    L.export_links_raw(a.data_ptr(), n_doubles)
+    L.export_links_raw(b.data_ptr(), n_doubles)
     t0 = time.perf_counter()
-    orc.update_pass(B, BETA, orc.OVERRELAX, 2, 1, step, 1, 0, n_slab)
+    orc.update_pass(A, BETA, orc.OVERRELAX, 2, 1, step, 1, 0, n_slab)
     t_or = time.perf_counter() - t0
     n_or = per_pass
     or_err = float(slab_diff(A, B).max())
@@ -258,7 +292,7 @@ def oracle_leg(L, n_doubles, target_seconds=12.0, max_slices=24):
     while t_hb + t_or < target_seconds and k < 64:
         mu, par = (k // 2) % 4, k % 2
         t0 = time.perf_counter()
-        orc.update_pass(B, BETA, orc.HEATBATH if k % 2 == 0 else orc.OVERRELAX, mu, par, step + 1, 1, 0, n_slab)
+        orc.update_pass(A, BETA, orc.HEATBATH if k % 2 == 0 else orc.OVERRELAX, mu, par, step + 1, 1, 0, n_slab)
         if k % 2 == 0:
             t_hb += time.perf_counter() - t0
             n_hb += per_pass
@@ -268,10 +302,11 @@ def oracle_leg(L, n_doubles, target_seconds=12.0, max_slices=24):
         k += 1
     r_hb, r_or = n_hb / t_hb, n_or / t_or
     r = (N_HB + N_OR) / (N_HB / r_hb + N_OR / r_or)
-    desc = (f"FP64 oracle on the GPU's configuration after the timed sweeps: heatbath and overrelaxation passes "
-            f"over time slices [0,{n_slab}) of the 48^3x96 lattice ({per_pass} link updates per pass), "
-            f"{n_hb} heatbath updates in {t_hb:.1f} s, {n_or} overrelaxation updates in {t_or:.1f} s, rates "
-            f"combined 1:5 as in a sweep; plaquette of the whole lattice in {t_plaq:.1f} s")
+    desc = (f"FP64 oracle on its own thermalised 48^3x96 configuration (16^3x32, six sweeps from a cold start, "
+            f"tiled 3x3x3x3; made in {t_input:.1f} s): heatbath and overrelaxation passes over time slices "
+            f"[0,{n_slab}) ({per_pass} link updates per pass), {n_hb} heatbath updates in {t_hb:.1f} s, {n_or} "
+            f"overrelaxation updates in {t_or:.1f} s, rates combined 1:5 as in a sweep; plaquette of the whole "
+            f"lattice in {t_plaq:.1f} s")
     agreement = {
         "plaquette": {"gpu": p_gpu, "oracle": p_orc, "abs_err": abs(p_gpu - p_orc)},
         "polyakov": {"gpu": [l_gpu.real, l_gpu.imag], "oracle": [l_orc.real, l_orc.imag],
@@ -279,8 +314,8 @@ def oracle_leg(L, n_doubles, target_seconds=12.0, max_slices=24):
         "overrelaxation_pass": {"links": 4 * per_pass, "max_abs_err": or_err, "bound": 1e-5},
         "heatbath_pass": {"links": 4 * per_pass, "max_abs_err_where_branches_agree": hb_err,
                           "branch_flips": flips, "bound": "1e-5, flips <= 1e-6 of updates"},
-        "note": "one pass from the same FP64 input; links of all four directions on the slab compared "
-                "(only direction 1 / 2 changes)",
+        "note": "the GPU lattice loaded with the oracle's configuration; one pass from the same input; links of all "
+                "four directions on the slab compared (only direction 1 / 2 changes)",
     }
     del A, B, a, b
     return {"value": r, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": desc,
@@ -356,7 +391,6 @@ def run_sweeps(L, steps):
 
 
 def gpu_arm(args):
-    import numpy as np
     import torch
     import paper_1112_4533_gb300 as sun
 
@@ -464,6 +498,19 @@ def gpu_arm(args):
         cpu = oracle_leg(L, 8 * NC * NC * V, args.cpu_seconds)
 
     L.close()
+    del L
+    torch.cuda.empty_cache()
+    extra = {}
+    if rank == 0 and world == 1 and not args.no_extra:
+        for name, fn in [("c1_su2_8x8x8x8_fp64", lambda: measure_c1(local)),
+                         ("c2_su3_16x16x16x16_fp32", lambda: measure_c2(local)),
+                         ("c4_batched_64_chains", lambda: measure_batched(local, steps=3)),
+                         ("c5_serving", lambda: measure_serving(local, n_requests=args.requests,
+                                                                budget_gb=args.budget_gb))]:
+            t0 = time.perf_counter()
+            extra[name] = fn()
+            extra[name]["measure_s"] = time.perf_counter() - t0
+            torch.cuda.empty_cache()
     # kernels per sweep: the passes (8 per step, or 4 wavefront launches with bit 8), the separate
     # re-unitarization (placement 0 only), plaquette, Polyakov loop, step counter
     passes_per_step = 4 if (args.variant & 8) and not (args.variant & 18) else 8
@@ -481,16 +528,11 @@ def gpu_arm(args):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic (cold start, Philox seed 1 + rank)",
-        "config": {"workload": WORKLOAD_NAME, "nc": NC, "dims": list(DIMS), "beta": BETA,
-                   "n_heatbath": N_HB, "n_overrelax": N_OR, "storage_reals": args.storage,
-                   "kernel_variant": args.variant, "block_threads": args.block,
-                   "autotuned": tuned,
-                   "reunitarize": ("FP64, every link once per sweep, " +
-                                   {0: "own pass after the sweep", 1: "in the update kernels of the last step",
-                                    2: "spread over the steps"}[args.reunit_mode]),
-                   "observables": "FP64 plaquette + Polyakov every sweep",
-                   "link_updates_per_step": updates_per_sweep(),
-                   "l2": "lattice (2.0 GB) larger than L2, no flush", "parallelism": f"replicas x{world}"},
+        "config": workload_config(world),
+        "kernel_config": {"storage_reals": args.storage, "kernel_variant": args.variant, "block_threads": args.block,
+                          "graph_sweeps": args.graph_sweeps, "autotuned": tuned,
+                          "reunit_placement": {0: "own pass after the sweep", 1: "in the update kernels of the last "
+                                               "step", 2: "spread over the steps"}[args.reunit_mode]},
         "hbm_gbs_effective": updates_per_sweep() * 9 * link_bytes / (ms_max / K / 1e3) / 1e9,
         "plaquette_last": float(plaq[-1]),
         "polyakov_last": [float(poly[-1].real), float(poly[-1].imag)],
@@ -505,6 +547,7 @@ def gpu_arm(args):
         "cpu_baseline": cpu,
         "clocks": clocks,
         "gpu_launches": launches_per_sweep * K,
+        "workloads": extra,
     }
     if rank == 0:
         print(json.dumps(out))
@@ -513,104 +556,315 @@ def gpu_arm(args):
         dist.destroy_process_group()
 
 
-def batched_arm(args):
+# ------------------------------------------------- the other workloads ----
+# C1, C2 (single chains shaped like the paper's runs), C4 (64 chains batched)
+# and C5 (served request stream), measured in the default run beside the
+# headline, each with CUDA-event timing and its own clock record.
+
+def _timed(stream, fn):
+    """Run fn() between two CUDA events on stream; returns (ms, fn's result)."""
+    import torch
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    r = fn()
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b), r
+
+
+def measure_c1(local, reps=20):
+    """SU(2) 8^4, beta 2.3, cold start, 10 sweeps of 1 heatbath + 4
+    overrelaxation, FP64 quaternion links, Philox seed 1, plaquette after every
+    sweep (the sweep re-unitarizes).  One run = the 10 sweeps from the cold
+    start; its plaquette history is compared with the FP64 oracle's, both
+    free-running and sweep by sweep from the oracle's links."""
+    import numpy as np
+    import oracle as orc
+    import paper_1112_4533_gb300 as sun
+
+    dims, beta, sweeps = (8, 8, 8, 8), 2.3, 10
+    L = sun.Lattice(2, dims, beta, hot_start=False, seed=1, precision=64, storage=4, graph_sweeps=sweeps)
+    cold = L.export_stored()
+    upd = sweeps * 5 * 4 * volume(dims)
+
+    def one_run():
+        L.import_stored(cold)
+        L.heatbath_step = 0
+        return _timed(L.stream, lambda: L.run(sweeps, 1, 4))
+
+    for _ in range(3):
+        one_run()
+    sampler = ClockSampler(gpu_selector(local))
+    sampler.start()
+    total, hist = 0.0, None
+    for _ in range(reps):
+        ms, (plaq, _) = one_run()
+        total += ms
+        hist = plaq
+    clocks = sampler.stop()
+    # the oracle's chain, and each GPU sweep from the oracle's links
+    U = orc.init(2, dims, False, 1)
+    o_hist, same = [], []
+    for s in range(sweeps):
+        L.import_links(U)
+        L.heatbath_step = s
+        p1, _ = L.run(1, 1, 4)
+        got = L.export_links()
+        orc.sweep(U, beta, 1, 4, True, 1, s)
+        o_hist.append(orc.plaquette(U))
+        same.append((abs(p1[0] - o_hist[-1]), float(np.abs(got - U).max())))
+    L.close()
+    o_hist = np.array(o_hist)
+    return {"metric": METRIC, "value": upd * reps / (total / 1e3), "unit": METRIC, "ms_per_run": total / reps,
+            "runs": reps, "link_updates_per_run": upd, "dtype": "f64",
+            "workload": "SU(2) 8^4 beta=2.3 cold start, 10 sweeps of 1 heatbath + 4 overrelaxation (re-unitarized), "
+                        "FP64 quaternion links, Philox seed 1, plaquette after each sweep",
+            "bound": "L2-resident (512 KiB of links): launch and latency bound",
+            "plaquette_history": [float(x) for x in hist],
+            "oracle_plaquette_history": [float(x) for x in o_hist],
+            "agreement": {
+                "same_input_max_abs_err_plaquette": max(a for a, _ in same),
+                "same_input_max_abs_err_links": max(b for _, b in same),
+                "free_running_abs_err_per_sweep": [float(x) for x in np.abs(hist - o_hist)],
+                "note": "same input: before each sweep the GPU lattice holds the oracle's links and heatbath step; "
+                        "free running: both chains from the cold start (rounding-order differences grow ~30x per "
+                        "sweep)"},
+            "clocks": clocks}
+
+
+def measure_c2(local, reps=3):
+    """SU(3) 16^4, beta 6.0, Haar start (seed 2), 200 sweeps of 1 heatbath + 4
+    overrelaxation, FP32 two-row links, FP64 re-unitarization every sweep and
+    FP64 plaquette after every sweep; the re-unitarization placement and kernel
+    shape measured by the autotuner.  Agreement: the first sweep from the
+    oracle's Haar start against the oracle's sweep."""
+    import numpy as np
+    import oracle as orc
+    import paper_1112_4533_gb300 as sun
+
+    dims, beta, sweeps = (16, 16, 16, 16), 6.0, 200
+    t = sun.autotune(3, dims, beta, 1, 4, precision=32, storage=12, reunit_mode=1, tune_storage=False,
+                     tune_reunit_mode=True)
+    kw = dict(precision=32, storage=12, variant=t["variant"], reunit_mode=t["reunit_mode"],
+              block_threads=t["block_threads"], graph_sweeps=t["graph_sweeps"])
+    L = sun.Lattice(3, dims, beta, hot_start=True, seed=2, **kw)
+    hot = L.export_stored()
+    upd = sweeps * 5 * 4 * volume(dims)
+
+    def one_run():
+        L.import_stored(hot)
+        L.heatbath_step = 0
+        return _timed(L.stream, lambda: L.run(sweeps, 1, 4, polyakov=False))
+
+    one_run()
+    sampler = ClockSampler(gpu_selector(local))
+    sampler.start()
+    total, hist = 0.0, None
+    for _ in range(reps):
+        ms, (plaq, _) = one_run()
+        total += ms
+        hist = plaq
+    clocks = sampler.stop()
+    U = orc.init(3, dims, True, 2)
+    L.import_links(U)
+    L.heatbath_step = 0
+    p1, _ = L.run(1, 1, 4, polyakov=False)
+    got = L.export_links()
+    L.close()
+    orc.sweep(U, beta, 1, 4, {0: True, 1: orc.REUNIT_FUSED, 2: orc.REUNIT_SPREAD}[kw["reunit_mode"]], 2, 0)
+    d = np.abs(got - U).reshape(-1, 9).max(axis=1)
+    tail = hist[100:]
+    bins = tail.reshape(10, -1).mean(axis=1)
+    return {"metric": METRIC, "value": upd * reps / (total / 1e3), "unit": METRIC, "ms_per_run": total / reps,
+            "ms_per_sweep": total / reps / sweeps, "runs": reps, "link_updates_per_run": upd, "dtype": "f32",
+            "workload": "SU(3) 16^4 beta=6.0 Haar start (seed 2), 200 sweeps of 1 heatbath + 4 overrelaxation, FP32 "
+                        "two-row links, FP64 re-unitarization every sweep, FP64 plaquette after each sweep",
+            "bound": "L2-resident (12 MiB of links)", "kernel_config": t,
+            "plaquette": {"first": float(hist[0]), "last": float(hist[-1]),
+                          "mean_sweeps_100_199": float(tail.mean()),
+                          "binned_err": float(bins.std(ddof=1) / np.sqrt(len(bins)))},
+            "agreement": {"first_sweep_abs_err_plaquette": abs(float(p1[0]) - orc.plaquette(U)),
+                          "first_sweep_max_abs_err_links": float(d.max()),
+                          "first_sweep_links_above_1e-5": int((d > 1e-5).sum()), "links": int(d.size),
+                          "note": "one sweep (40 passes, heatbath included) from the oracle's Haar start; a heatbath "
+                                  "branch flip would move its link and its neighbours' by O(1e-2)"},
+            "clocks": clocks}
+
+
+def c4_chains():
+    import numpy as np
+    rng = np.random.default_rng(4)
+    Ls = rng.choice([8, 12, 16, 24], size=64)
+    betas = rng.uniform(5.6, 6.4, size=64)
+    return [int(x) for x in Ls], [float(b) for b in betas]
+
+
+def measure_batched(local, steps=3, tune=True, opts=None):
+    """C4: 64 SU(3) chains, L drawn from {8,12,16,24}, beta uniform in
+    [5.6, 6.4], Haar starts (seeds 100..163), 50 sweeps of 1 heatbath + 4
+    overrelaxation each, FP32 update / FP64 re-unitarization, the shared kernel
+    configuration measured by the autotuner.  All 50 sweeps of all 64 chains
+    are one launch of a captured CUDA graph (per-pass kernels over all chains
+    of the group).  Plain path: the same chains one at a time, sun_run of 50
+    sweeps each (one graph launch per chain), same kernels.  Both timed with
+    CUDA events on one stream, after an untimed run of each."""
     import numpy as np
     import torch
     import paper_1112_4533_gb300 as sun
 
-    torch.cuda.set_device(0)
-    rng = np.random.default_rng(4)
-    n = 64
-    Ls = rng.choice([8, 12, 16, 24], size=n)
-    betas = rng.uniform(5.6, 6.4, size=n)
+    Ls, betas = c4_chains()
     sweeps = 50
     tuned = None
-    if not args.no_tune:
+    o = dict(storage=12, variant=1, reunit_mode=1, block_threads=0)
+    if opts:
+        o.update(opts)
+    if tune:
         t0 = time.perf_counter()
-        tuned = sun.autotune_batch([(3, (int(L),) * 4, float(b)) for L, b in zip(Ls, betas)], 1, 4, precision=32,
-                                   storage=args.storage, reunit_mode=args.reunit_mode, tune_storage=True,
+        tuned = sun.autotune_batch([(3, (L,) * 4, b) for L, b in zip(Ls, betas)], 1, 4, precision=32,
+                                   storage=o["storage"], reunit_mode=o["reunit_mode"], tune_storage=True,
                                    tune_reunit_mode=True)
         tuned["tuning_s"] = time.perf_counter() - t0
-        args.storage, args.variant, args.reunit_mode = tuned["storage"], tuned["variant"], tuned["reunit_mode"]
-        args.block, args.graph_sweeps = tuned["block_threads"], tuned["graph_sweeps"]
-    kw = dict(precision=32, storage=args.storage, reunit_mode=args.reunit_mode, variant=args.variant,
-              block_threads=args.block, graph_sweeps=args.graph_sweeps)
-    lats = [sun.Lattice(3, (int(L),) * 4, float(b), hot_start=True, seed=100 + i, **kw)
+        o.update({k: tuned[k] for k in ("storage", "variant", "reunit_mode", "block_threads")})
+    kw = dict(precision=32, graph_sweeps=sweeps, **o)
+    stream = torch.cuda.Stream()
+    lats = [sun.Lattice(3, (L,) * 4, b, hot_start=True, seed=100 + i, stream=stream, **kw)
             for i, (L, b) in enumerate(zip(Ls, betas))]
-    updates = sum((1 + 4) * 4 * int(L) ** 4 for L in Ls) * sweeps
-    B = sun.Batch(lats, use_graphs=True)
-    B.run(max(1, args.warmup), 1, 4)
-    torch.cuda.synchronize()
-    t = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        B.run(sweeps, 1, 4)
-        t.append(time.perf_counter() - t0)
+    starts = [L.export_stored() for L in lats]
+
+    def reset():
+        for L, h in zip(lats, starts):
+            L.import_stored(h)
+            L.heatbath_step = 0
+
+    updates = sum(5 * 4 * L ** 4 for L in Ls) * sweeps
+    B = sun.Batch(lats, stream=stream, use_graphs=True)
+    reset()
+    B.run(sweeps, 1, 4)  # captures the 50-sweep graph
+    sampler = ClockSampler(gpu_selector(local))
+    sampler.start()
+    tb = []
+    for _ in range(steps):
+        reset()
+        ms, (plaq_b, _) = _timed(stream, lambda: B.run(sweeps, 1, 4))
+        tb.append(ms)
+    clocks = sampler.stop()
     B.close()
-    # plain path: the same chains, one at a time
+    # plain: each chain alone
+    reset()
     for L in lats:
-        L.run(1, 1, 4)
-    torch.cuda.synchronize()
+        L.run(sweeps, 1, 4)  # captures each chain's 50-sweep graph
+
+    def plain():
+        return [L.run(sweeps, 1, 4)[0] for L in lats]
+
+    sampler = ClockSampler(gpu_selector(local))
+    sampler.start()
     tp = []
-    for _ in range(max(1, args.steps // 2)):
-        t0 = time.perf_counter()
-        for L in lats:
-            L.run(sweeps, 1, 4)
-        torch.cuda.synchronize()
-        tp.append(time.perf_counter() - t0)
+    for _ in range(steps):
+        reset()
+        ms, plaq_p = _timed(stream, plain)
+        tp.append(ms)
+    clocks_p = sampler.stop()
     for L in lats:
         L.close()
-    tb, tpl = min(t), min(tp)
-    out = {"metric": "batched chains/s", "value": n / tb, "unit": "chains/s", "n_gpus": 1, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": tb * 1e3, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32", "data": "synthetic (Haar starts, seeds 100..163)",
-           "config": {"workload": "64 SU(3) chains, L in {8,12,16,24} (seeded draw), beta U[5.6,6.4], hot start, "
-                                  "50 sweeps of 1 heatbath + 4 overrelaxation each, FP32 links",
-                      "L_counts": {str(v): int((Ls == v).sum()) for v in (8, 12, 16, 24)},
-                      "link_updates_per_step": updates, "storage_reals": args.storage, "kernel_variant": args.variant,
-                      "block_threads": args.block, "reunit_mode": args.reunit_mode, "autotuned": tuned},
-           "link_updates_per_s": updates / tb,
-           # per batch sweep of the one SU(3) group: 40 passes, the separate re-unitarization
-           # (placement 0), plaquette and Polyakov partials and their per-chain sums, two counters
-           "gpu_launches": args.steps * sweeps * (40 + (1 if args.reunit_mode == 0 else 0) + 4 + 2),
-           "plain": {"value": n / tpl, "unit": "chains/s", "ms_per_step": tpl * 1e3, "link_updates_per_s": updates / tpl,
-                     "path": "each chain alone, sun_run of 50 sweeps (one captured sweep graph per chain)"},
-           "speedup_vs_plain": tpl / tb}
+    # links evolve bitwise as alone; the batch sums each chain's plaquette in its
+    # own fixed order, so the histories agree to rounding
+    hist_diff = max(float(np.abs(plaq_b[:, i] - plaq_p[i]).max()) for i in range(len(lats)))
+    mb, mp = min(tb), min(tp)
+    return {"metric": "chains/s", "value": 64 / (mb / 1e3), "unit": "chains/s", "ms_per_step": mb,
+            "steps": steps, "link_updates_per_s": updates / (mb / 1e3), "link_updates_per_step": updates,
+            "dtype": "f32",
+            "workload": "64 SU(3) chains, L in {8,12,16,24} (seeded draw), beta U[5.6,6.4], Haar start, 50 sweeps of "
+                        "1 heatbath + 4 overrelaxation each, FP32 links, FP64 re-unitarization every sweep",
+            "L_counts": {str(v): Ls.count(v) for v in (8, 12, 16, 24)},
+            "kernel_config": dict(o, graph_sweeps=sweeps, autotuned=tuned),
+            "launch": "all 50 sweeps of all 64 chains: one launch of one captured CUDA graph",
+            "plain": {"value": 64 / (mp / 1e3), "unit": "chains/s", "ms_per_step": mp,
+                      "link_updates_per_s": updates / (mp / 1e3), "clocks": clocks_p,
+                      "path": "each chain alone: sun_run of 50 sweeps (one graph launch per chain), same kernels"},
+            "speedup_vs_plain": mp / mb,
+            "plaquette_histories_max_abs_diff_vs_plain": hist_diff,
+            "clocks": clocks}
+
+
+def measure_serving(local, n_requests=80, budget_gb=64.0, policy="srpt", tick_ms=40.0, work_cap_ms=3.0,
+                    sweeps_per_tick=None):
+    """C5: a Poisson request trace (mean 20/s, seed 7) of SU(Nc) chains, Nc in
+    {2,3,4,6}, L in {8..24}, 20..200 sweeps each, served by continuous batching
+    under a device-memory budget; against the same trace served one request at
+    a time, in arrival order (FIFO) and shortest request first (SRPT), so that
+    the scheduling gain and the batching gain show separately.  Each path's
+    wall time is the interval between two CUDA events on the default stream
+    around the whole trace (the server synchronises after every tick)."""
+    import torch
+    from paper_1112_4533_gb300 import serve
+
+    trace = serve.poisson_trace(n_requests, rate=20.0, seed=7)
+    budget = int(budget_gb * (1 << 30))
+    warm = serve.poisson_trace(4, rate=50.0, seed=99, Ls=(8,), sweeps=(2, 3))
+    serve.Server(budget).run(warm)
+    serve.serve_plain(warm)
+    upd = sum(r.n_sweeps * 5 * 4 * r.L ** 4 for r in trace)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, fn in [("served", lambda: serve.Server(budget, sweeps_per_tick=sweeps_per_tick,
+                                                     work_cap_ms=work_cap_ms, tick_ms=tick_ms,
+                                                     policy=policy).run(trace)),
+                     ("plain_fifo", lambda: serve.serve_plain(trace, order="fifo")[0]),
+                     ("plain_srpt", lambda: serve.serve_plain(trace, order="srpt")[0])]:
+        sampler = ClockSampler(gpu_selector(local))
+        sampler.start()
+        ms, res = _timed(stream, fn)
+        clocks = sampler.stop()
+        st = serve.latency_stats(res)
+        out[name] = {"p50_s": st["p50_s"], "p99_s": st["p99_s"], "mean_s": st["mean_s"],
+                     "completed": st["completed"], "wall_s": ms / 1e3, "requests_per_s": len(trace) / (ms / 1e3),
+                     "link_updates_per_s": upd / (ms / 1e3), "clocks": clocks}
+    s, pf, ps = out["served"], out["plain_fifo"], out["plain_srpt"]
+    return {"metric": "requests/s", "value": s["requests_per_s"], "unit": "requests/s",
+            "p50_s": s["p50_s"], "p99_s": s["p99_s"], "dtype": "f32",
+            "workload": f"{n_requests} requests, Poisson mean 20/s (seed 7), Nc in {{2,3,4,6}}, L in "
+                        "{8,12,16,20,24}, 20..200 sweeps of 1 heatbath + 4 overrelaxation, FP32 links",
+            "server": {"hbm_budget_gb": budget_gb, "policy": policy, "tick_ms": tick_ms, "work_cap_ms": work_cap_ms},
+            "link_updates": upd, "served": s, "plain_fifo": pf, "plain_srpt": ps,
+            "throughput_vs_plain_fifo": s["requests_per_s"] / pf["requests_per_s"],
+            "throughput_vs_plain_srpt": s["requests_per_s"] / ps["requests_per_s"],
+            "note": "plain_fifo: one request at a time in arrival order; plain_srpt: one at a time, the arrived "
+                    "request with the least work first (scheduling without batching); served: continuous batching"}
+
+
+def batched_arm(args):
+    """--workload batched: the C4 measurement alone, as its own JSON line."""
+    import torch
+    torch.cuda.set_device(0)
+    opts = None
+    if args.no_tune:
+        opts = dict(storage=args.storage, variant=args.variant, reunit_mode=args.reunit_mode,
+                    block_threads=args.block)
+    r = measure_batched(0, steps=max(1, args.steps), tune=not args.no_tune, opts=opts)
+    out = {"metric": "batched chains/s", "value": r["value"], "unit": "chains/s", "n_gpus": 1,
+           "steps": r["steps"], "warmup": 1, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (Haar starts, seeds 100..163)",
+           "config": {"workload": r["workload"], "L_counts": r["L_counts"],
+                      "link_updates_per_step": r["link_updates_per_step"]},
+           "gpu_launches": None, "clocks": r["clocks"], "batched": r}
     print(json.dumps(out))
 
 
 def serving_arm(args):
+    """--workload serving: the C5 measurement alone, as its own JSON line."""
     import torch
-    from paper_1112_4533_gb300 import serve
-
     torch.cuda.set_device(0)
-    trace = serve.poisson_trace(args.requests, rate=20.0, seed=7)
-    budget = int(args.budget_gb * (1 << 30))
-    warm = serve.poisson_trace(4, rate=50.0, seed=99, Ls=(8,), sweeps=(2, 3))
-    serve.Server(budget).run(warm)  # load kernels
-    srv = serve.Server(budget, sweeps_per_tick=args.sweeps_per_tick or None, work_cap_ms=args.work_cap_ms,
-                       tick_ms=args.tick_ms, policy=args.policy)
-    t0 = time.perf_counter()
-    out = srv.run(trace)
-    wall = time.perf_counter() - t0
-    st = serve.latency_stats(out)
-    plain, pwall, pupd = serve.serve_plain(trace)
-    pst = serve.latency_stats(plain)
-    upd = sum(r.n_sweeps * 5 * 4 * r.L ** 4 for r in trace)
-    res = {"metric": "p50 request latency", "value": st["p50_s"], "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 1,
-           "ms_per_step": wall * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f32", "data": "synthetic Poisson trace (seed 7)",
-           "config": {"workload": f"{args.requests} requests, Poisson mean 20/s, Nc in {{2,3,4,6}}, L in "
-                                  "{8,12,16,20,24}, 20..200 sweeps of 1 heatbath + 4 overrelaxation, FP32",
-                      "hbm_budget_gb": args.budget_gb, "max_sweeps_per_tick": args.sweeps_per_tick or None,
-                      "tick_ms": args.tick_ms, "work_cap_ms": args.work_cap_ms, "policy": args.policy},
-           "p99_s": st["p99_s"], "mean_s": st["mean_s"], "completed": st["completed"],
-           "throughput": {"requests_per_s": len(trace) / wall, "link_updates_per_s": upd / wall},
-           "plain": {"p50_s": pst["p50_s"], "p99_s": pst["p99_s"], "mean_s": pst["mean_s"],
-                     "requests_per_s": len(trace) / pwall, "link_updates_per_s": pupd / pwall,
-                     "path": "one request at a time in arrival order, sun_run per chain"},
-           "ticks": srv.ticks}
-    print(json.dumps(res))
+    r = measure_serving(0, n_requests=args.requests, budget_gb=args.budget_gb, policy=args.policy,
+                        tick_ms=args.tick_ms, work_cap_ms=args.work_cap_ms,
+                        sweeps_per_tick=args.sweeps_per_tick or None)
+    out = {"metric": "served requests/s", "value": r["value"], "unit": "requests/s", "n_gpus": 1, "steps": 1,
+           "warmup": 1, "ms_per_step": r["served"]["wall_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic Poisson trace (seed 7)",
+           "config": {"workload": r["workload"]}, "gpu_launches": None, "clocks": r["served"]["clocks"],
+           "serving": r}
+    print(json.dumps(out))
 
 
 def reference_arm(args):
@@ -631,8 +885,7 @@ def reference_arm(args):
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus, "steps": K,
            "warmup": W, "ms_per_step": dt / K * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic (cold start)",
-           "config": {"workload": WORKLOAD_NAME, "nc": NC, "dims": list(DIMS), "beta": BETA,
-                      "n_heatbath": N_HB, "n_overrelax": N_OR},
+           "config": workload_config(args.gpus),
            "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": desc},
            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
@@ -655,6 +908,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="fixed configuration from the flags, no autotuning")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the C1, C2, batched (C4) and serving (C5) measurements of the default run")
     ap.add_argument("--block", type=int, default=0, help="threads per block of the update kernels (0 = 128)")
     ap.add_argument("--graph-sweeps", type=int, default=0, help="sweeps captured per CUDA graph (0 = 1)")
     ap.add_argument("--workload", choices=["single", "batched", "serving"], default="single")

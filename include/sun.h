@@ -158,6 +158,13 @@ void sun_lattice_destroy(sun_lattice* lat); /* syncs; NULL is a no-op */
  * (SUN_OVERRELAX, Eq. 17 per subgroup).  Does not advance the step counter. */
 sun_status sun_update_pass(sun_lattice* lat, int mode, int mu, int parity);
 
+/* The same pass with each updated link re-unitarized in FP64 (Sec. 2, as
+ * sun_reunitarize) right after its update, inside the update kernel: the
+ * placement reunit_mode 1 uses for the links of a sweep's last step.  Links
+ * not updated by the pass are left as they are.  SUN_ERR_UNSUPPORTED where
+ * reunit_mode 1 is not built (FP64 with Nc >= 5). */
+sun_status sun_update_pass_reunit(sun_lattice* lat, int mode, int mu, int parity);
+
 /* One sweep: n_heatbath heatbath steps then n_overrelax overrelaxation steps, a step
  * being the eight passes mu = 0..3 x (even, odd); then re-unitarization if this is a
  * reunit_every-th sweep.  Heatbath step s of the sweep uses counter value c + s,
@@ -381,15 +388,15 @@ sun_status sun_autotune_batch(int n, const int* nc, const int* dims, const doubl
 /* Plaquette of link storage the caller already holds, with no allocation.
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate device memory when they measure -- code confined to a memory
- * arena it does not own, code enqueuing work while a stream is captured into a
- * CUDA graph, latency-critical loops that cannot afford an allocation's
- * implicit synchronisation.
+ * arena it does not own (a framework that hands out fixed buffers and forbids
+ * cudaMalloc after start-up), latency-critical loops that cannot afford an
+ * allocation's implicit synchronisation.
  *  links      device address of link storage in this library's layout (e.g.
  *             sun_lattice_info.links of a lattice with the same nc, dims,
  *             precision, storage); read only
  *  nc, dims, precision, storage  as for sun_lattice_create (storage 0 = default)
- *  out        device address of one double that receives <P> (Eq. 4 normalised
- *             as sun_plaquette); the caller owns it
+ *  out        device address of one double that receives <P>, normalised as
+ *             sun_plaquette; the caller owns it
  *  stream     cudaStream_t to enqueue on (NULL = the legacy default stream); the
  *             call is asynchronous and does not synchronise
  * Calls no cudaMalloc, cudaFree or allocating library routine.  The reduction

@@ -389,6 +389,19 @@ sun_status sun_update_pass(sun_lattice* L, int mode, int mu, int parity) {
   return check_launch(L->ops->pass(ctx_on(L, L->stream), mode, mu, parity, 0u, 0u, 0u), "update pass");
 }
 
+sun_status sun_update_pass_reunit(sun_lattice* L, int mode, int mu, int parity) {
+  if (!L) return fail(SUN_ERR_ARG, "lattice is NULL");
+  if (mode != SUN_HEATBATH && mode != SUN_OVERRELAX) return fail(SUN_ERR_ARG, "mode must be 0 or 1");
+  if (mu < 0 || mu > 3) return fail(SUN_ERR_ARG, "mu must be in 0..3");
+  if (parity != 0 && parity != 1) return fail(SUN_ERR_ARG, "parity must be 0 or 1");
+  if (!L->ops->fused_reunit)
+    return fail(SUN_ERR_UNSUPPORTED, "the fused re-unitarization is not built for nc = %d at precision %d", L->nc,
+                L->precision);
+  SUN_TRY(set_device(L));
+  // reunit_mod 1, remainder 0: every run of 32 half-sites, i.e. every updated link
+  return check_launch(L->ops->pass(ctx_on(L, L->stream), mode, mu, parity, 0u, 1u, 0u), "update pass");
+}
+
 sun_status sun_sweep(sun_lattice* L, int n_hb, int n_or) {
   if (!L) return fail(SUN_ERR_ARG, "lattice is NULL");
   if (n_hb < 0 || n_or < 0) return fail(SUN_ERR_ARG, "step counts must be >= 0");

@@ -2,9 +2,7 @@
 //
 // Some callers cannot allocate device memory when they need an observable:
 // code that runs inside a memory arena it does not own (a framework that hands
-// out fixed buffers and forbids cudaMalloc after start-up), code that enqueues
-// work while a stream is being captured into a CUDA graph (cudaMalloc is not a
-// stream operation and breaks or invalidates the capture), and latency-critical
+// out fixed buffers and forbids cudaMalloc after start-up), and latency-critical
 // loops where an allocation's implicit synchronisation is not acceptable.
 // sun_plaquette_noalloc serves them: it reads links the caller already holds
 // (in this library's storage layout) and writes the result to a caller-owned

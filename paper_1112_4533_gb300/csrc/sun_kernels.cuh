@@ -239,6 +239,20 @@ __device__ __forceinline__ Rows2<R> load_rows2(const char* blk, int64_t Vh, int6
   return m;
 }
 
+#ifdef SUN_PREFETCH_NEXT
+// request the stored components of half-site h of a block into L1
+template <class R, int N, int S>
+__device__ __forceinline__ void prefetch_link(const char* blk, int64_t Vh, int64_t h) {
+  constexpr int nreals = Layout<R, N, S>::nreals;
+  constexpr int n16 = nreals / (16 / int(sizeof(R)));
+#pragma unroll
+  for (int c = 0; c < n16; ++c) {
+    const char* q = blk + (int64_t(c) * Vh + h) * 16;
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(q));
+  }
+}
+#endif
+
 // U_nu(x) U_mu(x+nu) U_nu(x+mu)^+ added to st; BL: how U_mu is loaded
 template <class R, int N, int S, bool ROWS2, int BL>
 __device__ __forceinline__ void staple_forward(Mat<R, N>& st, const char* pa, int64_t ha, const char* pb, int64_t hb,
@@ -361,9 +375,33 @@ __device__ __forceinline__ void pass_body(const PassParams& p, int par, int64_t 
   constexpr int BL = COH ? kLoadCg : kLoadNc;  // U_mu of the other parity
   Mat<R, N> st;
   mat_zero(st);
+#ifdef SUN_PREFETCH_NEXT
+  // the links of the next direction's two staple terms are requested into L1
+  // one direction ahead, so that their latency overlaps this direction's products
+  auto prefetch_terms = [&](int nu) {
+    const int cnu = s.c[nu];
+    const uint32_t lex_pnu = fwd(g, lex, cnu, nu);
+    const uint32_t lex_mnu = bwd(g, lex, cnu, nu);
+    const uint32_t lex_mnu_pmu = fwd(g, lex_mnu, cmu, mu);
+    prefetch_link<R, N, S>(block_ptr(p, nu, par), g.Vh, h);
+    prefetch_link<R, N, S>(block_ptr(p, mu, opp), g.Vh, lex_pnu >> 1);
+    prefetch_link<R, N, S>(block_ptr(p, nu, opp), g.Vh, lex_pmu >> 1);
+    prefetch_link<R, N, S>(block_ptr(p, nu, opp), g.Vh, lex_mnu >> 1);
+    prefetch_link<R, N, S>(block_ptr(p, mu, opp), g.Vh, lex_mnu >> 1);
+    prefetch_link<R, N, S>(block_ptr(p, nu, par), g.Vh, lex_mnu_pmu >> 1);
+  };
+  prefetch_terms(mu == 0 ? 1 : 0);
+#endif
 #pragma unroll
   for (int nu = 0; nu < 4; ++nu) {
     if (nu == mu) continue;
+#ifdef SUN_PREFETCH_NEXT
+    {
+      int nx = nu + 1;
+      if (nx == mu) ++nx;
+      if (nx < 4) prefetch_terms(nx);
+    }
+#endif
     const int cnu = s.c[nu];
     const uint32_t lex_pnu = fwd(g, lex, cnu, nu);
     const uint32_t lex_mnu = bwd(g, lex, cnu, nu);
@@ -927,7 +965,7 @@ __device__ __forceinline__ uint64_t global_timer_ns() {
 }
 
 // Thread 0: wait until the even slices t-1, t, t+1 are finished.  The wait is
-// bounded; one that gives up is counted in sync[2] and the unit goes ahead.
+// bounded; one that gives up is counted in sync[0] and the unit goes ahead.
 __device__ __forceinline__ void wave_wait_even(const WaveParams& w, uint32_t t) {
   const uint32_t ts[3] = {t == 0 ? w.nt - 1 : t - 1, t, t + 1 == w.nt ? 0u : t + 1};
   uint64_t t0 = 0;
@@ -1220,8 +1258,9 @@ __global__ void __launch_bounds__(256) init_kernel(const LinkParams p) {
 
 // ---------------------------------------------------------------------------
 // Deterministic FP64 reductions: per-thread sums -> warp shuffles -> block ->
-// one partial per block; the last block to finish adds the partials in block
-// order and writes the scaled result, then re-arms the counter.
+// one partial per block; the last block to finish adds the partials in a
+// fixed order (lane l sums partials l, l + 32, ..., then a warp shuffle tree)
+// and writes the scaled result, then re-arms the counter.
 // ---------------------------------------------------------------------------
 struct ReduceParams {
   double* partials;      // [gridDim.x * K]

@@ -12,7 +12,7 @@ are on the GPU join at the next tick; finished chains leave and free their
 memory.  A chain's results do not depend on which ticks and batches it ran in.
 
 The plain path (serve_plain) runs the same trace one request at a time, each
-chain alone (sun_run), in arrival order.
+chain alone (sun_run), in arrival order or shortest request first.
 """
 import dataclasses
 import time
@@ -194,15 +194,28 @@ class Server:
         return reqs
 
 
-def serve_plain(trace: List[Request], n_overrelax=4, precision=32, clock=time.perf_counter):
-    """One request at a time, in arrival order, each chain alone (sun_run)."""
+def serve_plain(trace: List[Request], n_overrelax=4, precision=32, clock=time.perf_counter, order="fifo"):
+    """One request at a time, each chain alone (sun_run).  order "fifo" takes
+    requests in arrival order; "srpt" takes, among the requests that have
+    arrived, the one with the least predicted work (sweeps x sweep time), as
+    the server's policy does, but without batching or preemption."""
+    if order not in ("fifo", "srpt"):
+        raise ValueError("order must be 'fifo' or 'srpt'")
     reqs = _clone(trace)
+    queue = sorted(reqs, key=lambda q: q.arrival)
     t0 = clock()
     updates = 0
-    for r in sorted(reqs, key=lambda q: q.arrival):
+    while queue:
         now = clock() - t0
-        if r.arrival > now:
-            time.sleep(r.arrival - now)
+        if queue[0].arrival > now:
+            time.sleep(queue[0].arrival - now)
+            now = clock() - t0
+        if order == "srpt":
+            arrived = [q for q in queue if q.arrival <= now]
+            r = min(arrived, key=lambda q: (q.n_sweeps * sweep_cost_ms(q), q.arrival))
+        else:
+            r = queue[0]
+        queue.remove(r)
         r.t_admit = clock() - t0
         with sun.Lattice(r.nc, r.dims, r.beta, hot_start=True, seed=r.seed, precision=precision) as lat:
             plaq, poly = lat.run(r.n_sweeps, 1, n_overrelax)

@@ -65,6 +65,7 @@ SIGNATURES = [
                                           ctypes.c_uint64, ctypes.POINTER(Options)]),
     ("sun_lattice_destroy", None, [_P]),
     ("sun_update_pass", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    ("sun_update_pass_reunit", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     ("sun_sweep", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     ("sun_run", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D]),
     ("sun_reunitarize", ctypes.c_int, [_P]),
@@ -285,6 +286,10 @@ class Lattice:
     # -- the method
     def update_pass(self, mode, mu, parity):
         _check(self._lib.sun_update_pass(self.handle, int(mode), int(mu), int(parity)))
+
+    def update_pass_reunit(self, mode, mu, parity):
+        """update_pass with each updated link re-unitarized in FP64 inside the kernel."""
+        _check(self._lib.sun_update_pass_reunit(self.handle, int(mode), int(mu), int(parity)))
 
     def sweep(self, n_heatbath=1, n_overrelax=4):
         _check(self._lib.sun_sweep(self.handle, int(n_heatbath), int(n_overrelax)))

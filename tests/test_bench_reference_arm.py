@@ -37,3 +37,14 @@ def test_reference_arm_other_ranks_exit_without_work():
     r = run_bench({"RANK": "1", "WORLD_SIZE": "2"})
     assert r.returncode == 0, r.stderr
     assert not [l for l in r.stdout.splitlines() if l.startswith("{")]
+
+
+def test_both_arms_describe_the_same_workload():
+    """The reference arm's config is the workload description the GPU arm prints."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    r = run_bench()
+    d = json.loads([l for l in r.stdout.splitlines() if l.startswith("{")][0])
+    assert d["config"] == bench.workload_config(1)

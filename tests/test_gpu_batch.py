@@ -77,7 +77,10 @@ def test_batch_graph_replay_equals_direct_launches(sunlib):
 def test_fp64_batch_matches_oracle(sunlib):
     specs = [(2, (4, 4, 4, 6), 2.3, 21, 4, 64), (3, (4, 6, 4, 4), 6.0, 22, 18, 64)]
     lats = [make(sunlib, s) for s in specs]
-    starts = [L.export_links() for L in lats]
+    # the oracle's own Haar starts, loaded into the chains
+    starts = [orc.init(s[0], s[1], True, s[3]) for s in specs]
+    for L, U in zip(lats, starts):
+        L.import_links(U)
     with sunlib.Batch(lats) as B:
         plaq, _ = B.run(1, 1, 1)
     for i, (L, s) in enumerate(zip(lats, specs)):

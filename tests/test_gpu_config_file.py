@@ -105,3 +105,51 @@ def test_compact_host_format(sunlib, nc, st, prec):
         L.run(1, 1, 1)
         L.import_stored_raw(pinned.data_ptr(), raw.nbytes)
         assert np.array_equal(L.export_links(), U)
+
+
+@pytest.mark.parametrize("nc,st,prec", [(3, 12, 64), (3, 18, 64), (2, 4, 64), (4, 32, 64), (3, 12, 32),
+                                        (2, 4, 32)])
+def test_loaded_configuration_follows_the_oracle(sunlib, tmp_path, nc, st, prec):
+    """A file written from the oracle's links (loaded into a lattice with
+    heatbath step 3) holds exactly those links (rounded to FP32 for FP32
+    lattices) in the rows the storage keeps; loaded into a fresh lattice of
+    another seed, beta and start, the chain continues as the oracle does from
+    the same links and state: FP64, one sweep of 1 heatbath + 2
+    overrelaxation steps with the re-unitarization, links to 1e-11; FP32, one
+    overrelaxation pass (1e-5) and, from the file again, one heatbath pass
+    (1e-5 where the accept branch agrees, no flips at this size)."""
+    import oracle as orc
+    from tests.oracle_configs import cold_thermal
+    dims = (4, 4, 6, 4)
+    beta, seed, step = beta_for(nc), 21, 3
+    U = cold_thermal(nc, dims, beta)
+    path = tmp_path / "oracle.cfg"
+    with sunlib.Lattice(nc, dims, beta, seed=seed, storage=st, precision=prec) as A:
+        A.import_links(U)
+        A.heatbath_step = step
+        A.save(path)
+    rows = st // (2 * nc)
+    payload = np.fromfile(str(path), dtype=np.uint8)[128:].view(np.complex128 if prec == 64 else np.complex64)
+    want_rows = U[..., :rows, :].astype(np.complex128 if prec == 64 else np.complex64)
+    assert np.array_equal(payload, want_rows.ravel())
+    with sunlib.Lattice(nc, dims, 1.0, hot_start=False, seed=99, storage=st, precision=prec) as C:
+        C.load(path)
+        assert C.heatbath_step == step
+        if prec == 64:
+            C.sweep(1, 2)
+            got = C.export_links()
+            want = U.copy()
+            orc.sweep(want, beta, 1, 2, True, seed, step)
+            assert np.abs(got - want).max() < 1e-11
+        else:
+            C.update_pass(sunlib.OVERRELAX, 1, 0)
+            got = C.export_links()
+            want = U.copy()
+            orc.update_pass(want, beta, orc.OVERRELAX, 1, 0, step, seed)
+            assert np.abs(got - want).max() < 1e-5
+            C.load(path)
+            C.update_pass(sunlib.HEATBATH, 2, 1)
+            got = C.export_links()
+            want = U.copy()
+            orc.update_pass(want, beta, orc.HEATBATH, 2, 1, step, seed)
+            assert np.abs(got - want).max() < 1e-5

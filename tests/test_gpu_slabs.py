@@ -74,3 +74,28 @@ def test_slab_arguments_are_checked(sunlib):
     for n in (3, 8, 0):
         with pytest.raises(sunlib.SunError):
             sunlib.Slabs(3, (4, 4, 4, 8), n, 6.0)
+
+
+@pytest.mark.parametrize("nc,st,prec,n_hb,n_or", [(3, 18, 64, 1, 2), (3, 12, 64, 1, 2), (2, 4, 64, 1, 2),
+                                                  (3, 12, 32, 0, 1)])
+@pytest.mark.parametrize("n_slabs", [2, 4])
+def test_slabs_follow_the_oracle(sunlib, nc, st, prec, n_hb, n_or, n_slabs):
+    """The oracle's cold-start-thermalised configuration loaded into 2 or 4
+    slabs; one sweep with the halo exchange after every pass and the
+    re-unitarization, against the oracle's sweep of the whole lattice from the
+    same links: FP64 links to 1e-11 (a heatbath and two overrelaxation steps),
+    FP32 links to 1e-5 (one overrelaxation step: no accept/reject branch);
+    the plaquette and Polyakov loop of the result against the oracle's."""
+    import oracle as orc
+    from tests.oracle_configs import cold_thermal
+    dims = (4, 6, 4, 8)
+    beta = beta_for(nc)
+    U = cold_thermal(nc, dims, beta)
+    with sunlib.Slabs(nc, dims, n_slabs, beta, hot_start=False, seed=23, storage=st, precision=prec) as S:
+        S.import_links(U)
+        p, l = S.run(1, n_hb, n_or)
+        got = S.export_links()
+    orc.sweep(U, beta, n_hb, n_or, True, 23, 0)
+    assert np.abs(got - U).max() < (1e-11 if prec == 64 else 1e-5)
+    assert abs(p[0] - orc.plaquette(U)) < (1e-12 if prec == 64 else 2e-6)
+    assert abs(l[0] - orc.polyakov(U)) < (1e-12 if prec == 64 else 2e-5)
