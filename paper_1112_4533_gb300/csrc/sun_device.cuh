@@ -211,124 +211,6 @@ __device__ __forceinline__ Mat<R, N> mul_nd(const Mat<R, N>& a, const Mat<R, N>&
   return c;
 }
 
-#ifdef SUN_PACKED_CPLX
-// ------------------------------------------ packed 3x3 complex products ----
-// SU(3) products in FP32 with the complex multiply-adds on packed pairs: a
-// complex entry (re, im) is one f32x2 value, and each packed FMA does the two
-// scalar FMAs of cmul / cfma / cfmac / ccfma that share an operand, with that
-// operand broadcast.  Every lane is the scalar operation on the same operands
-// in the same order (a product with a negated operand is the negated product,
-// exactly), so these overloads compute bitwise what the generic templates do.
-__device__ __forceinline__ F2 cpack(Cpx<float> a) { return f2_pack(a.re, a.im); }
-__device__ __forceinline__ Cpx<float> cunpack(F2 v) {
-  Cpx<float> c;
-  f2_unpack(v, c.re, c.im);
-  return c;
-}
-
-// C = A B: per k, lanes (re, im) take fma(a.re, b.re | b.im) then fma(a.im, -b.im | b.re)
-__device__ __forceinline__ Mat<float, 3> mul_nn(const Mat<float, 3>& a, const Mat<float, 3>& b) {
-  F2 bp[3][3], bs[3][3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      bp[k][j] = cpack(b.e[k][j]);
-      bs[k][j] = f2_pack(-b.e[k][j].im, b.e[k][j].re);
-    }
-  Mat<float, 3> c;
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      F2 s = F2(a.e[i][0].im) * bs[0][j];
-      s = fma(F2(a.e[i][0].re), bp[0][j], s);
-#pragma unroll
-      for (int k = 1; k < 3; ++k) {
-        s = fma(F2(a.e[i][k].re), bp[k][j], s);
-        s = fma(F2(a.e[i][k].im), bs[k][j], s);
-      }
-      c.e[i][j] = cunpack(s);
-    }
-  return c;
-}
-
-// C += A B^+: per k, lanes take fma(a.re | a.im, b.re) then fma(a.im | -a.re, b.im)
-__device__ __forceinline__ void acc_nd(Mat<float, 3>& c, const Mat<float, 3>& a, const Mat<float, 3>& b) {
-  F2 ap[3][3], as[3][3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      ap[i][k] = cpack(a.e[i][k]);
-      as[i][k] = f2_pack(a.e[i][k].im, -a.e[i][k].re);
-    }
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      F2 s = cpack(c.e[i][j]);
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        s = fma(ap[i][k], F2(b.e[j][k].re), s);
-        s = fma(as[i][k], F2(b.e[j][k].im), s);
-      }
-      c.e[i][j] = cunpack(s);
-    }
-}
-
-// C += A B
-__device__ __forceinline__ void acc_nn(Mat<float, 3>& c, const Mat<float, 3>& a, const Mat<float, 3>& b) {
-  F2 bp[3][3], bs[3][3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      bp[k][j] = cpack(b.e[k][j]);
-      bs[k][j] = f2_pack(-b.e[k][j].im, b.e[k][j].re);
-    }
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      F2 s = cpack(c.e[i][j]);
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        s = fma(F2(a.e[i][k].re), bp[k][j], s);
-        s = fma(F2(a.e[i][k].im), bs[k][j], s);
-      }
-      c.e[i][j] = cunpack(s);
-    }
-}
-
-// C = A^+ B: per k, lanes take fma(a.re, b.re | b.im) then fma(a.im, b.im | -b.re)
-__device__ __forceinline__ Mat<float, 3> mul_dn(const Mat<float, 3>& a, const Mat<float, 3>& b) {
-  F2 bp[3][3], bn[3][3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      bp[k][j] = cpack(b.e[k][j]);
-      bn[k][j] = f2_pack(b.e[k][j].im, -b.e[k][j].re);
-    }
-  Mat<float, 3> c;
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      F2 s = F2(a.e[0][i].im) * bn[0][j];
-      s = fma(F2(a.e[0][i].re), bp[0][j], s);
-#pragma unroll
-      for (int k = 1; k < 3; ++k) {
-        s = fma(F2(a.e[k][i].re), bp[k][j], s);
-        s = fma(F2(a.e[k][i].im), bn[k][j], s);
-      }
-      c.e[i][j] = cunpack(s);
-    }
-  return c;
-}
-#endif  // SUN_PACKED_CPLX
-
 // Re Tr(A B^+) = sum_ij Re(a_ij conj(b_ij))
 template <class R, int N>
 __device__ __forceinline__ R retr_nd(const Mat<R, N>& a, const Mat<R, N>& b) {

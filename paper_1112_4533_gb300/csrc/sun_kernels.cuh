@@ -239,20 +239,6 @@ __device__ __forceinline__ Rows2<R> load_rows2(const char* blk, int64_t Vh, int6
   return m;
 }
 
-#ifdef SUN_PREFETCH_NEXT
-// request the stored components of half-site h of a block into L1
-template <class R, int N, int S>
-__device__ __forceinline__ void prefetch_link(const char* blk, int64_t Vh, int64_t h) {
-  constexpr int nreals = Layout<R, N, S>::nreals;
-  constexpr int n16 = nreals / (16 / int(sizeof(R)));
-#pragma unroll
-  for (int c = 0; c < n16; ++c) {
-    const char* q = blk + (int64_t(c) * Vh + h) * 16;
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(q));
-  }
-}
-#endif
-
 // U_nu(x) U_mu(x+nu) U_nu(x+mu)^+ added to st; BL: how U_mu is loaded
 template <class R, int N, int S, bool ROWS2, int BL>
 __device__ __forceinline__ void staple_forward(Mat<R, N>& st, const char* pa, int64_t ha, const char* pb, int64_t hb,
@@ -375,33 +361,9 @@ __device__ __forceinline__ void pass_body(const PassParams& p, int par, int64_t 
   constexpr int BL = COH ? kLoadCg : kLoadNc;  // U_mu of the other parity
   Mat<R, N> st;
   mat_zero(st);
-#ifdef SUN_PREFETCH_NEXT
-  // the links of the next direction's two staple terms are requested into L1
-  // one direction ahead, so that their latency overlaps this direction's products
-  auto prefetch_terms = [&](int nu) {
-    const int cnu = s.c[nu];
-    const uint32_t lex_pnu = fwd(g, lex, cnu, nu);
-    const uint32_t lex_mnu = bwd(g, lex, cnu, nu);
-    const uint32_t lex_mnu_pmu = fwd(g, lex_mnu, cmu, mu);
-    prefetch_link<R, N, S>(block_ptr(p, nu, par), g.Vh, h);
-    prefetch_link<R, N, S>(block_ptr(p, mu, opp), g.Vh, lex_pnu >> 1);
-    prefetch_link<R, N, S>(block_ptr(p, nu, opp), g.Vh, lex_pmu >> 1);
-    prefetch_link<R, N, S>(block_ptr(p, nu, opp), g.Vh, lex_mnu >> 1);
-    prefetch_link<R, N, S>(block_ptr(p, mu, opp), g.Vh, lex_mnu >> 1);
-    prefetch_link<R, N, S>(block_ptr(p, nu, par), g.Vh, lex_mnu_pmu >> 1);
-  };
-  prefetch_terms(mu == 0 ? 1 : 0);
-#endif
 #pragma unroll
   for (int nu = 0; nu < 4; ++nu) {
     if (nu == mu) continue;
-#ifdef SUN_PREFETCH_NEXT
-    {
-      int nx = nu + 1;
-      if (nx == mu) ++nx;
-      if (nx < 4) prefetch_terms(nx);
-    }
-#endif
     const int cnu = s.c[nu];
     const uint32_t lex_pnu = fwd(g, lex, cnu, nu);
     const uint32_t lex_mnu = bwd(g, lex, cnu, nu);
@@ -491,23 +453,14 @@ __global__ void __launch_bounds__(128, occ_blocks<N>()) update_pass_mat_occ(cons
 // ---------------------------------------------------------------------------
 template <class R, int N>
 struct Group {
-  static constexpr int LPW = 32 / N;          // links per warp
+  // rows per lane: SU(6) FP32 lanes own two rows (and two columns), so that every
+  // operand read from shared memory feeds two complex multiply-adds
+  static constexpr int RB = (N == 6 && sizeof(R) == 4) ? 2 : 1;
+  static constexpr int LPL = N / RB;          // lanes per link
+  static constexpr int LPW = 32 / LPL;        // links per warp
   static constexpr int WARPS = 4;             // warps per block (128 threads)
   static constexpr int LPB = WARPS * LPW;     // links per block
-  static constexpr int SLOTS = (32 + N - 1) / N;  // link slots per warp in shared memory
   static constexpr int CPR = 2 * N * int(sizeof(R)) / 16;  // 16-byte components per row
-};
-
-// Shared memory of one link slot: three N x N staging matrices, padded so that
-// consecutive slots start 4 banks apart.  The lanes of a warp read the same
-// entry of their own slot's matrix in one instruction, so the warp's 5 to 8 slots
-// then hit different banks instead of colliding every 32 / gcd words.
-template <class R, int N>
-struct alignas(16) GroupSlot {
-  static constexpr int kWords = 3 * N * N * 2 * int(sizeof(R)) / 4;
-  static constexpr int kPadWords = ((4 - kWords % 32) % 32 + 32) % 32;
-  Cpx<R> m[3][N][N];
-  uint32_t pad[kPadWords > 0 ? kPadWords : 1];
 };
 
 template <class R, int N>
@@ -580,35 +533,41 @@ __device__ __forceinline__ void smem_put_row(Cpx<R> (*m)[N], int r, const Cpx<R>
   for (int k = 0; k < N; ++k) m[r][k] = row[k];
 }
 
-// heatbath element of one subgroup drawn by the Nc lanes of a group at once
-template <class R, int N>
+// heatbath element of one subgroup drawn by the LANES lanes of a link at once:
+// lane q of the link tries attempts round * LANES * PER + q * PER + t, t < PER,
+// stopping at its first accepted one, and the link takes the first accepted
+// attempt in attempt order, so the draw is that of one attempt at a time
+template <class R, int LANES, int PER>
 __device__ __forceinline__ bool heatbath_su2_group(R alpha, bool skip, uint2 key, uint32_t link, uint32_t step,
-                                                   uint32_t sub, int r, int base, Quat<R>& b) {
+                                                   uint32_t sub, int q, int base, Quat<R>& b) {
   const bool kp = alpha >= R(1.5);
   const R inv2a = R(1) / (R(2) * alpha);
   const R e = -d_expm1(R(-2) * alpha);
   bool found = skip;
   bool got = false;
   R b0 = R(1);
-  for (int round = 0; round * N < kHeatbathAttempts; ++round) {
-    const int att = round * N + r;
+  for (int round = 0; round * LANES * PER < kHeatbathAttempts; ++round) {
     bool acc = false;
     R x = R(1);
-    if (!found && att < kHeatbathAttempts) {
-      const uint4 u = philox4x32_10(make_uint4(link, step, (sub << 16) | uint32_t(att), kTagHeatbath), key);
-      const R r0 = u01<R>(u.x), r1 = u01<R>(u.y), r2 = u01<R>(u.z), r3 = u01<R>(u.w);
-      if (kp) {
-        const R c = d_cospi(R(2) * r1);
-        const R delta = -(d_log(r0) + c * c * d_log(r2)) * inv2a;
-        acc = r3 * r3 <= R(1) - delta;
-        x = R(1) - R(2) * delta;
-      } else {
-        x = alpha > R(0) ? R(1) + d_log1p(-r0 * e) / alpha : R(1) - R(2) * r0;
-        acc = r1 * r1 <= R(1) - x * x;
+#pragma unroll
+    for (int t = 0; t < PER; ++t) {
+      const int att = (round * LANES + q) * PER + t;
+      if (!found && !acc && att < kHeatbathAttempts) {
+        const uint4 u = philox4x32_10(make_uint4(link, step, (sub << 16) | uint32_t(att), kTagHeatbath), key);
+        const R r0 = u01<R>(u.x), r1 = u01<R>(u.y), r2 = u01<R>(u.z), r3 = u01<R>(u.w);
+        if (kp) {
+          const R c = d_cospi(R(2) * r1);
+          const R delta = -(d_log(r0) + c * c * d_log(r2)) * inv2a;
+          acc = r3 * r3 <= R(1) - delta;
+          x = R(1) - R(2) * delta;
+        } else {
+          x = alpha > R(0) ? R(1) + d_log1p(-r0 * e) / alpha : R(1) - R(2) * r0;
+          acc = r1 * r1 <= R(1) - x * x;
+        }
       }
     }
     const unsigned bal = __ballot_sync(0xffffffffu, acc);
-    const unsigned mine = (base < 32 ? (bal >> base) : 0u) & ((1u << N) - 1u);
+    const unsigned mine = (base < 32 ? (bal >> base) : 0u) & ((1u << LANES) - 1u);
     const int first = mine ? __ffs(mine) - 1 : 0;
     const R xb = __shfl_sync(0xffffffffu, x, (base + first) & 31);
     if (!found && mine) {
@@ -632,19 +591,100 @@ __device__ __forceinline__ bool heatbath_su2_group(R alpha, bool skip, uint2 key
   return true;
 }
 
+// ---------------------------------------------------------------------------
+// Block-wide staging of the row-parallel pass.  The LPB links of a block sit at
+// LPB consecutive half-sites, and so do their neighbours of each role in a
+// staple term (up to the lattice's periodic wrap).  The block loads the three
+// neighbour links of a term for all its links together, consecutive threads
+// taking consecutive 16-byte components of one component array (runs of LPB x
+// 16 bytes instead of a warp load spread over Nc component arrays), straight
+// into shared memory (cp.async); the lanes then read their rows there.  A link
+// has a slot of an odd number of 16-byte quads, so that eight consecutive
+// slots start in eight different bank quads.  The update's own links are read
+// and written the same way.
+// ---------------------------------------------------------------------------
+template <class R, int N>
+struct GroupTile {
+  static constexpr int LPB = Group<R, N>::LPB;
+  static constexpr int C16 = N * Group<R, N>::CPR;         // 16-byte components of a link
+  static constexpr int kQuads = (C16 & 1) == 0 ? C16 + 1 : C16;
+  static constexpr int kSlotBytes = kQuads * 16;
+  static constexpr int kSlots = LPB + 1;                   // + one for lanes past a warp's last whole link
+  static constexpr int kBytes = 3 * kSlots * kSlotBytes;
+};
+
+template <class R, int N>
+__device__ __forceinline__ Cpx<R> (*tile_mat(char* tile, int q, int slot))[N] {
+  return reinterpret_cast<Cpx<R>(*)[N]>(tile + (q * GroupTile<R, N>::kSlots + slot) * GroupTile<R, N>::kSlotBytes);
+}
+
+// Load NQ links (roles q < NQ, at half-sites hidx[q][j] of block pointers b[q])
+// of every link j of the block into the tile; cached in L2 only (cp.async.cg),
+// so it also serves links this kernel writes afterwards.  Thread t takes link
+// j = t % LPB and components t / LPB, + G, + 2G, ... (G threads per link), so
+// that consecutive threads read consecutive components of one array.  Ends with
+// the block synchronised.
+template <class R, int N, int NQ>
+__device__ __forceinline__ void group_stage(char* tile, const uint32_t (*hidx)[GroupTile<R, N>::LPB], const char* b0,
+                                            const char* b1, const char* b2, int64_t Vh) {
+  using T = GroupTile<R, N>;
+  constexpr int G = 128 / T::LPB;
+  constexpr int PER = (T::C16 + G - 1) / G;
+  const int j = int(threadIdx.x) % T::LPB, g = int(threadIdx.x) / T::LPB;
+  if (g < G) {
+    const int64_t cstep = int64_t(G) * Vh * 16;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const char* blk = q == 0 ? b0 : (q == 1 ? b1 : b2);
+      const char* src = blk + (int64_t(g) * Vh + hidx[q][j]) * 16;
+      const uint32_t dst = uint32_t(__cvta_generic_to_shared(tile + (q * T::kSlots + j) * T::kSlotBytes + g * 16));
+#pragma unroll
+      for (int m = 0; m < PER; ++m) {
+        if (PER * G == T::C16 || g + m * G < T::C16)
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + uint32_t(m * G * 16)),
+                       "l"(src + m * cstep)
+                       : "memory");
+      }
+    }
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  __syncthreads();
+}
+
 template <class R, int N, int MODE>
-__device__ __forceinline__ void group_pass_body(const PassParams& p, int64_t h, bool active, int r, int base,
-                                                Cpx<R> (*sm)[N][N]) {
+__device__ __forceinline__ void group_pass_body(const PassParams& p, int64_t first_link, int64_t h_end, char* tile,
+                                                uint32_t (*hidx)[GroupTile<R, N>::LPB]) {
+  using T = GroupTile<R, N>;
+  using G = Group<R, N>;
+  constexpr int RB = G::RB, LPL = G::LPL;
   const Geom& g = p.g;
   const int mu = p.mu, par = p.parity, opp = par ^ 1;
+  // lane -> (link j of the block, lane q of the link: rows and columns q RB .. q RB + RB - 1);
+  // lanes past a warp's last whole link use the spare slot, run a copy of a real
+  // link and never store
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gi = lane / LPL;
+  const int q = lane - gi * LPL;
+  const int base = gi * LPL;
+  const bool whole = gi < G::LPW;
+  const int j = warp * G::LPW + gi;
+  const int slot = whole ? j : T::LPB;
+  const int64_t link = first_link + j;
+  const bool active = whole && link < h_end;
+  const int64_t h = link < h_end ? link : h_end - 1;
+  const int n_act = int(h_end - first_link < T::LPB ? h_end - first_link : T::LPB);
+
   const Site s = decode_half(g, h, par);
   const uint32_t lex = uint32_t(s.lex);
   const int cmu = coord_of(s, mu);
   const uint32_t lex_pmu = fwd(g, lex, cmu, mu);
+  const bool writer = whole && q == 0;
 
-  Cpx<R> st[N];
+  Cpx<R> st[RB][N];
 #pragma unroll
-  for (int k = 0; k < N; ++k) st[k] = {R(0), R(0)};
+  for (int t = 0; t < RB; ++t)
+#pragma unroll
+    for (int k = 0; k < N; ++k) st[t][k] = {R(0), R(0)};
 #pragma unroll
   for (int nu = 0; nu < 4; ++nu) {
     if (nu == mu) continue;
@@ -652,84 +692,171 @@ __device__ __forceinline__ void group_pass_body(const PassParams& p, int64_t h, 
     const uint32_t lex_pnu = fwd(g, lex, cnu, nu);
     const uint32_t lex_mnu = bwd(g, lex, cnu, nu);
     const uint32_t lex_mnu_pmu = fwd(g, lex_mnu, cmu, mu);
-    {  // U_nu(x) U_mu(x+nu) U_nu(x+mu)^+ : row r of a, then (a B) C^+
-      Cpx<R> a[N], row[N];
-      load_row<R, N>(block_ptr(p, nu, par), g.Vh, h, r, a);
-      load_row<R, N>(block_ptr(p, mu, opp), g.Vh, lex_pnu >> 1, r, row);
-      smem_put_row<R, N>(sm[0], r, row);
-      load_row<R, N>(block_ptr(p, nu, opp), g.Vh, lex_pmu >> 1, r, row);
-      smem_put_row<R, N>(sm[1], r, row);
-      __syncwarp();
-      Cpx<R> ab[N];
+    {  // U_nu(x) U_mu(x+nu) U_nu(x+mu)^+ : rows q RB + t of (A B) C^+
+      if (writer) {
+        hidx[0][j] = uint32_t(h);
+        hidx[1][j] = lex_pnu >> 1;
+        hidx[2][j] = lex_pmu >> 1;
+      }
+      __syncthreads();
+      group_stage<R, N, 3>(tile, hidx, block_ptr(p, nu, par), block_ptr(p, mu, opp), block_ptr(p, nu, opp), g.Vh);
+      const Cpx<R>(*A)[N] = tile_mat<R, N>(tile, 0, slot);
+      const Cpx<R>(*B)[N] = tile_mat<R, N>(tile, 1, slot);
+      const Cpx<R>(*C)[N] = tile_mat<R, N>(tile, 2, slot);
+      Cpx<R> ar[RB][N], ab[RB][N];
 #pragma unroll
-      for (int j = 0; j < N; ++j) {
-        Cpx<R> x = cmul(a[0], sm[0][0][j]);
+      for (int t = 0; t < RB; ++t)
 #pragma unroll
-        for (int k = 1; k < N; ++k) cfma(x, a[k], sm[0][k][j]);
-        ab[j] = x;
+        for (int k = 0; k < N; ++k) ar[t][k] = A[q * RB + t][k];
+#pragma unroll
+      for (int jj = 0; jj < N; ++jj) {
+        {
+          const Cpx<R> b = B[0][jj];
+#pragma unroll
+          for (int t = 0; t < RB; ++t) ab[t][jj] = cmul(ar[t][0], b);
+        }
+#pragma unroll
+        for (int k = 1; k < N; ++k) {
+          const Cpx<R> b = B[k][jj];
+#pragma unroll
+          for (int t = 0; t < RB; ++t) cfma(ab[t][jj], ar[t][k], b);
+        }
       }
 #pragma unroll
-      for (int j = 0; j < N; ++j) {
-        Cpx<R> x = cmulc(ab[0], sm[1][j][0]);
+      for (int jj = 0; jj < N; ++jj) {
+        Cpx<R> x[RB];
+        {
+          const Cpx<R> c = C[jj][0];
 #pragma unroll
-        for (int k = 1; k < N; ++k) cfmac(x, ab[k], sm[1][j][k]);
-        st[j].re += x.re;
-        st[j].im += x.im;
+          for (int t = 0; t < RB; ++t) x[t] = cmulc(ab[t][0], c);
+        }
+#pragma unroll
+        for (int k = 1; k < N; ++k) {
+          const Cpx<R> c = C[jj][k];
+#pragma unroll
+          for (int t = 0; t < RB; ++t) cfmac(x[t], ab[t][k], c);
+        }
+#pragma unroll
+        for (int t = 0; t < RB; ++t) {
+          st[t][jj].re += x[t].re;
+          st[t][jj].im += x[t].im;
+        }
       }
-      __syncwarp();
+      __syncthreads();
     }
-    {  // U_nu(x-nu)^+ U_mu(x-nu) U_nu(x-nu+mu) : row r of A^+ (B C)
-      Cpx<R> b[N], row[N];
-      load_row<R, N>(block_ptr(p, nu, opp), g.Vh, lex_mnu >> 1, r, row);
-      smem_put_row<R, N>(sm[0], r, row);
-      load_row<R, N>(block_ptr(p, mu, opp), g.Vh, lex_mnu >> 1, r, b);
-      load_row<R, N>(block_ptr(p, nu, par), g.Vh, lex_mnu_pmu >> 1, r, row);
-      smem_put_row<R, N>(sm[1], r, row);
-      __syncwarp();
-      Cpx<R> bc[N];
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        Cpx<R> x = cmul(b[0], sm[1][0][j]);
-#pragma unroll
-        for (int k = 1; k < N; ++k) cfma(x, b[k], sm[1][k][j]);
-        bc[j] = x;
+    {  // U_nu(x-nu)^+ U_mu(x-nu) U_nu(x-nu+mu) : rows q RB + t of A^+ (B C)
+      if (writer) {
+        hidx[0][j] = lex_mnu >> 1;
+        hidx[1][j] = lex_mnu >> 1;
+        hidx[2][j] = lex_mnu_pmu >> 1;
       }
-      smem_put_row<R, N>(sm[2], r, bc);
-      __syncwarp();
+      __syncthreads();
+      group_stage<R, N, 3>(tile, hidx, block_ptr(p, nu, opp), block_ptr(p, mu, opp), block_ptr(p, nu, par), g.Vh);
+      const Cpx<R>(*A)[N] = tile_mat<R, N>(tile, 0, slot);
+      Cpx<R>(*B)[N] = tile_mat<R, N>(tile, 1, slot);
+      const Cpx<R>(*C)[N] = tile_mat<R, N>(tile, 2, slot);
+      Cpx<R> br[RB][N], bc[RB][N];
 #pragma unroll
-      for (int j = 0; j < N; ++j) {
-        Cpx<R> x = ccmul(sm[0][0][r], sm[2][0][j]);
+      for (int t = 0; t < RB; ++t)
 #pragma unroll
-        for (int k = 1; k < N; ++k) ccfma(x, sm[0][k][r], sm[2][k][j]);
-        st[j].re += x.re;
-        st[j].im += x.im;
+        for (int k = 0; k < N; ++k) br[t][k] = B[q * RB + t][k];
+#pragma unroll
+      for (int jj = 0; jj < N; ++jj) {
+        {
+          const Cpx<R> c = C[0][jj];
+#pragma unroll
+          for (int t = 0; t < RB; ++t) bc[t][jj] = cmul(br[t][0], c);
+        }
+#pragma unroll
+        for (int k = 1; k < N; ++k) {
+          const Cpx<R> c = C[k][jj];
+#pragma unroll
+          for (int t = 0; t < RB; ++t) cfma(bc[t][jj], br[t][k], c);
+        }
       }
+      // rows of B C replace the lane's rows of B, which only this lane reads
+#pragma unroll
+      for (int t = 0; t < RB; ++t)
+#pragma unroll
+        for (int jj = 0; jj < N; ++jj) B[q * RB + t][jj] = bc[t][jj];
       __syncwarp();
+      Cpx<R> ac[RB][N];  // column q RB + t of A
+#pragma unroll
+      for (int t = 0; t < RB; ++t)
+#pragma unroll
+        for (int k = 0; k < N; ++k) ac[t][k] = A[k][q * RB + t];
+#pragma unroll
+      for (int jj = 0; jj < N; ++jj) {
+        Cpx<R> x[RB];
+        {
+          const Cpx<R> v = B[0][jj];
+#pragma unroll
+          for (int t = 0; t < RB; ++t) x[t] = ccmul(ac[t][0], v);
+        }
+#pragma unroll
+        for (int k = 1; k < N; ++k) {
+          const Cpx<R> v = B[k][jj];
+#pragma unroll
+          for (int t = 0; t < RB; ++t) ccfma(x[t], ac[t][k], v);
+        }
+#pragma unroll
+        for (int t = 0; t < RB; ++t) {
+          st[t][jj].re += x[t].re;
+          st[t][jj].im += x[t].im;
+        }
+      }
+      __syncthreads();
     }
   }
 
-  // W = U Sigma^+ (row r), then columns of U and W for the subgroup updates
+  // the links being updated, U_mu(x) of this parity
   char* ublk = p.links + (2 * mu + par) * p.block_bytes;
-  Cpx<R> u[N], w[N];
-  load_row_rw<R, N>(ublk, g.Vh, h, r, u);
-  smem_put_row<R, N>(sm[0], r, st);
+  if (writer) hidx[0][j] = uint32_t(h);
+  __syncthreads();
+  group_stage<R, N, 1>(tile, hidx, ublk, ublk, ublk, g.Vh);
+  Cpx<R>(*U)[N] = tile_mat<R, N>(tile, 0, slot);
+  Cpx<R>(*S)[N] = tile_mat<R, N>(tile, 1, slot);
+  Cpx<R>(*Wm)[N] = tile_mat<R, N>(tile, 2, slot);
+  // W = U Sigma^+ (rows q RB + t), then columns of U and W for the subgroup updates
+#pragma unroll
+  for (int t = 0; t < RB; ++t)
+#pragma unroll
+    for (int k = 0; k < N; ++k) S[q * RB + t][k] = st[t][k];
   __syncwarp();
+  {
+    Cpx<R> ur[RB][N], w[RB][N];
 #pragma unroll
-  for (int j = 0; j < N; ++j) {
-    Cpx<R> x = cmulc(u[0], sm[0][j][0]);
+    for (int t = 0; t < RB; ++t)
 #pragma unroll
-    for (int k = 1; k < N; ++k) cfmac(x, u[k], sm[0][j][k]);
-    w[j] = x;
+      for (int k = 0; k < N; ++k) ur[t][k] = U[q * RB + t][k];
+#pragma unroll
+    for (int jj = 0; jj < N; ++jj) {
+      {
+        const Cpx<R> sv = S[jj][0];
+#pragma unroll
+        for (int t = 0; t < RB; ++t) w[t][jj] = cmulc(ur[t][0], sv);
+      }
+#pragma unroll
+      for (int k = 1; k < N; ++k) {
+        const Cpx<R> sv = S[jj][k];
+#pragma unroll
+        for (int t = 0; t < RB; ++t) cfmac(w[t][jj], ur[t][k], sv);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < RB; ++t)
+#pragma unroll
+      for (int k = 0; k < N; ++k) Wm[q * RB + t][k] = w[t][k];
   }
-  smem_put_row<R, N>(sm[1], r, u);
-  smem_put_row<R, N>(sm[2], r, w);
   __syncwarp();
-  Cpx<R> uc[N], wc[N];  // column r
+  Cpx<R> uc[RB][N], wc[RB][N];  // columns q RB + t
 #pragma unroll
-  for (int i = 0; i < N; ++i) {
-    uc[i] = sm[1][i][r];
-    wc[i] = sm[2][i][r];
-  }
+  for (int t = 0; t < RB; ++t)
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      uc[t][i] = U[i][q * RB + t];
+      wc[t][i] = Wm[i][q * RB + t];
+    }
   __syncwarp();
 
   uint32_t step = 0;
@@ -741,13 +868,14 @@ __device__ __forceinline__ void group_pass_body(const PassParams& p, int64_t h, 
 #pragma unroll
   for (int i = 0; i < N - 1; ++i) {
 #pragma unroll
-    for (int j = i + 1; j < N; ++j) {
-      const bool last = (i == N - 2) && (j == N - 1);
-      // W_ii, W_ji sit in lane i (column i), W_ij, W_jj in lane j (column j)
-      const Cpx<R> wii = {__shfl_sync(0xffffffffu, wc[i].re, (base + i) & 31), __shfl_sync(0xffffffffu, wc[i].im, (base + i) & 31)};
-      const Cpx<R> wji = {__shfl_sync(0xffffffffu, wc[j].re, (base + i) & 31), __shfl_sync(0xffffffffu, wc[j].im, (base + i) & 31)};
-      const Cpx<R> wij = {__shfl_sync(0xffffffffu, wc[i].re, (base + j) & 31), __shfl_sync(0xffffffffu, wc[i].im, (base + j) & 31)};
-      const Cpx<R> wjj = {__shfl_sync(0xffffffffu, wc[j].re, (base + j) & 31), __shfl_sync(0xffffffffu, wc[j].im, (base + j) & 31)};
+    for (int jn = i + 1; jn < N; ++jn) {
+      const bool last = (i == N - 2) && (jn == N - 1);
+      // column c sits in lane base + c / RB, register set c % RB
+      const int li = (base + i / RB) & 31, lj = (base + jn / RB) & 31;
+      const Cpx<R> wii = {__shfl_sync(0xffffffffu, wc[i % RB][i].re, li), __shfl_sync(0xffffffffu, wc[i % RB][i].im, li)};
+      const Cpx<R> wji = {__shfl_sync(0xffffffffu, wc[i % RB][jn].re, li), __shfl_sync(0xffffffffu, wc[i % RB][jn].im, li)};
+      const Cpx<R> wij = {__shfl_sync(0xffffffffu, wc[jn % RB][i].re, lj), __shfl_sync(0xffffffffu, wc[jn % RB][i].im, lj)};
+      const Cpx<R> wjj = {__shfl_sync(0xffffffffu, wc[jn % RB][jn].re, lj), __shfl_sync(0xffffffffu, wc[jn % RB][jn].im, lj)};
       const Quat<R> v = block_to_quat(wii, wij, wji, wjj);
       const R k = d_sqrt(fma(v.a0, v.a0, fma(v.a1, v.a1, fma(v.a2, v.a2, v.a3 * v.a3))));
       const bool ok = active && k > R(1e-15) && d_isfinite(k);
@@ -757,8 +885,8 @@ __device__ __forceinline__ void group_pass_body(const PassParams& p, int64_t h, 
       bool apply = ok;
       if constexpr (MODE == kHeatbathMode) {
         Quat<R> b;
-        const bool drawn = heatbath_su2_group<R, N>(ok ? alpha_coef * k : R(1), !ok, p.key, link_id, step,
-                                                    uint32_t(sub), r, base, b);
+        const bool drawn = heatbath_su2_group<R, LPL, RB>(ok ? alpha_coef * k : R(1), !ok, p.key, link_id, step,
+                                                          uint32_t(sub), q, base, b);
         apply = ok && drawn;
         a = qmul(b, vd);
       } else {
@@ -766,58 +894,55 @@ __device__ __forceinline__ void group_pass_body(const PassParams& p, int64_t h, 
       }
       if (apply) {
         const Cpx<R> A00 = {a.a0, a.a3}, A01 = {a.a2, a.a1}, A10 = {-a.a2, a.a1}, A11 = {a.a0, -a.a3};
-        Cpx<R> ni = cmul(A00, uc[i]), nj = cmul(A10, uc[i]);
-        cfma(ni, A01, uc[j]);
-        cfma(nj, A11, uc[j]);
-        uc[i] = ni;
-        uc[j] = nj;
-        if (!last) {
-          Cpx<R> mi = cmul(A00, wc[i]), mj = cmul(A10, wc[i]);
-          cfma(mi, A01, wc[j]);
-          cfma(mj, A11, wc[j]);
-          wc[i] = mi;
-          wc[j] = mj;
+#pragma unroll
+        for (int t = 0; t < RB; ++t) {
+          Cpx<R> ni = cmul(A00, uc[t][i]), nj = cmul(A10, uc[t][i]);
+          cfma(ni, A01, uc[t][jn]);
+          cfma(nj, A11, uc[t][jn]);
+          uc[t][i] = ni;
+          uc[t][jn] = nj;
+          if (!last) {
+            Cpx<R> mi = cmul(A00, wc[t][i]), mj = cmul(A10, wc[t][i]);
+            cfma(mi, A01, wc[t][jn]);
+            cfma(mj, A11, wc[t][jn]);
+            wc[t][i] = mi;
+            wc[t][jn] = mj;
+          }
         }
       }
       ++sub;
     }
   }
-  // back to rows and store
+  // back to rows in the tile, then the block stores its links' components
 #pragma unroll
-  for (int i = 0; i < N; ++i) sm[0][i][r] = uc[i];
-  __syncwarp();
-  if (active) {
-    Cpx<R> row[N];
+  for (int t = 0; t < RB; ++t)
 #pragma unroll
-    for (int k = 0; k < N; ++k) row[k] = sm[0][r][k];
-    store_row<R, N>(ublk, g.Vh, h, r, row);
+    for (int i = 0; i < N; ++i) U[i][q * RB + t] = uc[t][i];
+  __syncthreads();
+  {
+    constexpr int G = 128 / T::LPB;
+    constexpr int PER = (T::C16 + G - 1) / G;
+    using V = typename Vec16<R>::T;
+    const int jl = int(threadIdx.x) % T::LPB, gl = int(threadIdx.x) / T::LPB;
+    if (gl < G && jl < n_act) {
+      char* dst = ublk + (int64_t(gl) * g.Vh + hidx[0][jl]) * 16;
+      const char* src = tile + jl * T::kSlotBytes + gl * 16;
+      const int64_t cstep = int64_t(G) * g.Vh * 16;
+#pragma unroll
+      for (int m = 0; m < PER; ++m)
+        if (PER * G == T::C16 || gl + m * G < T::C16)
+          *reinterpret_cast<V*>(dst + m * cstep) = *reinterpret_cast<const V*>(src + m * G * 16);
+    }
   }
-}
-
-// block = 4 warps; warp w, lane l: link blockIdx.x * LPB + w * LPW + l / Nc, row l % Nc
-template <class R, int N>
-__device__ __forceinline__ void group_lane(int64_t first_link, int64_t Vh, int64_t& h, bool& active, int& r,
-                                           int& base, int& slot) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int gi = lane / N;
-  r = lane - gi * N;
-  base = gi * N;
-  slot = warp * Group<R, N>::SLOTS + gi;
-  const int64_t link = first_link + int64_t(warp) * Group<R, N>::LPW + gi;
-  active = gi < Group<R, N>::LPW && link < Vh;
-  h = link < Vh ? link : Vh - 1;
 }
 
 template <class R, int N, int MODE>
 // 5 resident blocks per SM: measured fastest for SU(6) FP32 (unbounded: 4 blocks,
 // 6 blocks: more spills); heatbath 6% and overrelaxation 2% faster than unbounded
 __global__ void __launch_bounds__(128, 5) update_pass_group(const PassParams p) {
-  __shared__ GroupSlot<R, N> sm[Group<R, N>::WARPS * Group<R, N>::SLOTS];
-  int64_t h;
-  bool active;
-  int r, base, slot;
-  group_lane<R, N>(p.h_begin + int64_t(blockIdx.x) * Group<R, N>::LPB, p.h_end, h, active, r, base, slot);
-  group_pass_body<R, N, MODE>(p, h, active, r, base, sm[slot].m);
+  __shared__ __align__(16) char tile[GroupTile<R, N>::kBytes];
+  __shared__ uint32_t hidx[3][GroupTile<R, N>::LPB];
+  group_pass_body<R, N, MODE>(p, p.h_begin + int64_t(blockIdx.x) * Group<R, N>::LPB, p.h_end, tile, hidx);
 }
 
 // FP64 passes of Nc >= 5 are built without the fused re-unitarization
@@ -1629,7 +1754,8 @@ __global__ void __launch_bounds__(128)
     update_pass_batch_group(const BatchParams bp, int mu, int parity, uint32_t step_offset) {
   __shared__ PassParams sp;
   __shared__ uint32_t first;
-  __shared__ GroupSlot<R, N> sm[Group<R, N>::WARPS * Group<R, N>::SLOTS];
+  __shared__ __align__(16) char tile[GroupTile<R, N>::kBytes];
+  __shared__ uint32_t hidx[3][GroupTile<R, N>::LPB];
   if (threadIdx.x == 0) {
     const int c = find_chain(bp.start, bp.n, blockIdx.x);
     const ChainDesc& d = bp.chains[c];
@@ -1651,12 +1777,8 @@ __global__ void __launch_bounds__(128)
     sp.v_global = uint32_t(d.g.V);
   }
   __syncthreads();
-  const PassParams p = sp;  // a private copy: the body's __syncwarp()s would force re-reads of shared memory
-  int64_t h;
-  bool active;
-  int r, base, slot;
-  group_lane<R, N>(int64_t(blockIdx.x - first) * Group<R, N>::LPB, p.g.Vh, h, active, r, base, slot);
-  group_pass_body<R, N, MODE>(p, h, active, r, base, sm[slot].m);
+  const PassParams p = sp;  // a private copy: the body's barriers would force re-reads of shared memory
+  group_pass_body<R, N, MODE>(p, int64_t(blockIdx.x - first) * Group<R, N>::LPB, p.g.Vh, tile, hidx);
 }
 
 // stage the chain's observable parameters of this block in shared memory

@@ -72,13 +72,34 @@ def footprint(req, precision=32):
 
 
 # Scheduling estimate of one sweep (1 heatbath + 4 overrelaxation, FP32), in ms
-# per lattice site, measured on GB300 on 24^4 lattices.
+# per lattice site: a default measured on a GB300 on 24^4 lattices, replaced by
+# measure_sweep_costs() on the GPU at hand.
 SWEEP_MS_PER_SITE = {2: 1.4e-6, 3: 4.2e-6, 4: 1.3e-5, 6: 6.7e-5}
 
 
-def sweep_cost_ms(req):
-    c = SWEEP_MS_PER_SITE.get(req.nc, 6.7e-5 * (req.nc / 6.0) ** 3)
+def sweep_cost_ms(req, costs=None):
+    table = SWEEP_MS_PER_SITE if costs is None else costs
+    c = table.get(req.nc, table.get(6, 6.7e-5) * (req.nc / 6.0) ** 3)
     return c * float(np.prod(req.dims))
+
+
+def measure_sweep_costs(ncs=(2, 3, 4, 6), L=24, sweeps=3, n_overrelax=4, precision=32):
+    """ms per lattice site of one sweep for each Nc, measured on the current GPU
+    (an L^4 lattice alone, after one untimed sweep; CUDA events on its stream)."""
+    import torch
+    out = {}
+    for nc in ncs:
+        beta = 2.3 if nc == 2 else 0.7 * nc * nc
+        with sun.Lattice(nc, (L,) * 4, beta, hot_start=True, seed=1, precision=precision) as lat:
+            lat.run(1, 1, n_overrelax, plaquette=False, polyakov=False)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(lat.stream)
+            lat.run(sweeps, 1, n_overrelax)
+            b.record(lat.stream)
+            b.synchronize()
+            out[nc] = a.elapsed_time(b) / sweeps / float(L ** 4)
+    return out
 
 
 class Server:
@@ -98,7 +119,8 @@ class Server:
     between its ticks, and leave as soon as they are done."""
 
     def __init__(self, hbm_budget, n_overrelax=4, sweeps_per_tick=None, precision=32, use_graphs=True,
-                 work_cap_ms=3.0, tick_ms=40.0, policy="srpt", graph_sweeps=16, clock=time.perf_counter):
+                 work_cap_ms=8.0, tick_ms=40.0, policy="srpt", graph_sweeps=16, clock=time.perf_counter,
+                 costs=None):
         if policy not in ("srpt", "fifo"):
             raise ValueError("policy must be 'srpt' or 'fifo'")
         self.work_cap = work_cap_ms
@@ -113,17 +135,19 @@ class Server:
         # sweeps of a few microseconds each
         self.graph_sweeps = int(graph_sweeps)
         self.clock = clock
+        self.costs = costs  # ms per site of a sweep by Nc (None: the default table)
         self.ticks = 0
         self.link_updates = 0
 
     def _select(self, active):
         if self.policy == "srpt":
-            order = sorted(active, key=lambda a: ((a[0].n_sweeps - a[2]) * sweep_cost_ms(a[0]), a[0].arrival))
+            order = sorted(active, key=lambda a: ((a[0].n_sweeps - a[2]) * sweep_cost_ms(a[0], self.costs),
+                                                  a[0].arrival))
         else:
             order = list(active)
         sel, cost = [], 0.0
         for a in order:
-            c = sweep_cost_ms(a[0])
+            c = sweep_cost_ms(a[0], self.costs)
             if sel and self.work_cap is not None and cost + c > self.work_cap:
                 continue
             sel.append(a)
@@ -194,7 +218,8 @@ class Server:
         return reqs
 
 
-def serve_plain(trace: List[Request], n_overrelax=4, precision=32, clock=time.perf_counter, order="fifo"):
+def serve_plain(trace: List[Request], n_overrelax=4, precision=32, clock=time.perf_counter, order="fifo",
+                costs=None):
     """One request at a time, each chain alone (sun_run).  order "fifo" takes
     requests in arrival order; "srpt" takes, among the requests that have
     arrived, the one with the least predicted work (sweeps x sweep time), as
@@ -212,7 +237,7 @@ def serve_plain(trace: List[Request], n_overrelax=4, precision=32, clock=time.pe
             now = clock() - t0
         if order == "srpt":
             arrived = [q for q in queue if q.arrival <= now]
-            r = min(arrived, key=lambda q: (q.n_sweeps * sweep_cost_ms(q), q.arrival))
+            r = min(arrived, key=lambda q: (q.n_sweeps * sweep_cost_ms(q, costs), q.arrival))
         else:
             r = queue[0]
         queue.remove(r)
