@@ -422,7 +422,7 @@ def gpu_arm(args):
     if not args.no_tune:
         t0 = time.perf_counter()
         tuned = sun.autotune(NC, DIMS, BETA, N_HB, N_OR, precision=32, storage=args.storage,
-                             reunit_mode=args.reunit_mode, tune_storage=True, tune_reunit_mode=True)
+                             reunit_mode=args.reunit_mode, tune_storage=True, tune_reunit_mode=True, two_row=True)
         tuned["tuning_s"] = time.perf_counter() - t0
         args.storage, args.variant, args.reunit_mode = tuned["storage"], tuned["variant"], tuned["reunit_mode"]
         args.block, args.graph_sweeps = tuned["block_threads"], tuned["graph_sweeps"]
@@ -455,8 +455,9 @@ def gpu_arm(args):
         del L
         torch.cuda.empty_cache()
         alt = 18 if args.storage == 12 else 12
+        other = "fp32_12real_full_staple" if args.variant & 2 else "fp32_12real_two_row_staple"
         for name, st, var in [(f"fp32_{alt}real", alt, args.variant & ~2),
-                              ("fp32_12real_two_row_staple", 12, (args.variant | 2) & ~8)]:
+                              (other, 12, (args.variant ^ 2) & ~8)]:
             if st == args.storage and var == args.variant:
                 continue
             L2 = sun.Lattice(NC, DIMS, BETA, hot_start=False, seed=1 + rank, storage=st,
@@ -470,9 +471,10 @@ def gpu_arm(args):
                 "variant": var, "ms_per_step": ms2 / k2s, "or_pass_ms": k2,
                 "or_pass_gbs": (V // 2) * 9 * L2.link_bytes / (k2 / 1e3) / 1e9}
             if var & 2:
-                variants[name]["note"] = ("third row of each staple term taken as conj(row0 x row1): "
-                                          "up to 1.2e-5 from the oracle on links of a Haar start before "
-                                          "their first re-unitarization (1e-5 bar)")
+                variants[name]["note"] = ("third row of each staple term taken as conj(row0 x row1), exact for "
+                                          "SU(3) products; within 1e-5 of the oracle on thermalised links")
+            else:
+                variants[name]["note"] = "every staple term multiplied out in full (all three rows)"
             L2.close()
             del L2
             torch.cuda.empty_cache()
@@ -981,8 +983,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--storage", type=int, default=12, choices=[12, 18])
-    ap.add_argument("--variant", type=int, default=1, choices=range(16),
-                    help="update-kernel variant bits: 1 = 5 blocks/SM register bound, 2 = two-row staple")
+    ap.add_argument("--variant", type=int, default=3, choices=range(32),
+                    help="update-kernel variant bits (with --no-tune): 1 = 5 blocks/SM register bound, "
+                         "2 = two-row staple products")
     ap.add_argument("--reunit-mode", type=int, default=1, choices=[0, 1, 2])
     ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--cpu-seconds", type=float, default=12.0,

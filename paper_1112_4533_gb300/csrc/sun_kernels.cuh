@@ -13,14 +13,17 @@ namespace sun {
 
 constexpr int kMaxBlockThreads = 256;
 // resident 128-thread blocks per SM the register-bounded kernels (variant bit 1)
-// are compiled for: 5 measured fastest among 5..8 for the SU(3) FP32 passes on
-// GB300 (more warps cost more spills than they hide latency)
+// are compiled for: 5 measured fastest among 4..8 for the SU(3) FP32 passes on
+// GB300 (more warps cost more spills than they hide latency); with the two-row
+// staple products (bit 2) the overrelaxation pass needs fewer registers and 6
+// blocks are faster (48^3 x 96: 0.533 -> 0.517 ms; its heatbath pass stays at 5)
 constexpr int kOccBlocks = 5;
+constexpr int kOccBlocksTwoRowOR = 6;
 // the same bound for the SU(4) FP32 per-link passes: 4 blocks (128 registers)
 constexpr int kOccBlocksSU4 = 4;
-template <int N>
+template <int N, int VAR = 1, int MODE = 0>
 __host__ __device__ constexpr int occ_blocks() {
-  return N == 4 ? kOccBlocksSU4 : kOccBlocks;
+  return N == 4 ? kOccBlocksSU4 : ((VAR & 2) != 0 && MODE == 1 ? kOccBlocksTwoRowOR : kOccBlocks);
 }
 constexpr int kHeatbathMode = 0;
 constexpr int kOverrelaxMode = 1;
@@ -422,7 +425,7 @@ __device__ __forceinline__ void pass_body(const PassParams& p, int par, int64_t 
   store_mat<R, N, S>(ublk, g.Vh, h, u);
 }
 
-// VAR bit 0: at most 128 threads per block and registers for occ_blocks<N>() blocks per SM;
+// VAR bit 0: at most 128 threads per block and registers for occ_blocks() blocks per SM;
 // VAR bit 1: two-row staple products (SU(3) two-row storage only).
 // REUNIT: the FP64 re-unitarization of selected links is compiled in (passes that
 // re-unitarize use this instantiation; the others carry no FP64 code).
@@ -434,7 +437,7 @@ __global__ void __launch_bounds__(kMaxBlockThreads) update_pass_mat(const PassPa
 }
 
 template <class R, int N, int S, int MODE, int VAR, bool REUNIT>
-__global__ void __launch_bounds__(128, occ_blocks<N>()) update_pass_mat_occ(const PassParams p) {
+__global__ void __launch_bounds__(128, (occ_blocks<N, VAR, MODE>())) update_pass_mat_occ(const PassParams p) {
   const int64_t h = p.h_begin + int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (h >= p.h_end) return;
   pass_body<R, N, S, MODE, (VAR & 2) != 0, REUNIT>(p, p.parity, h);
@@ -536,9 +539,10 @@ __device__ __forceinline__ void smem_put_row(Cpx<R> (*m)[N], int r, const Cpx<R>
 // heatbath element of one subgroup drawn by the LANES lanes of a link at once:
 // lane q of the link tries attempts round * LANES * PER + q * PER + t, t < PER,
 // stopping at its first accepted one, and the link takes the first accepted
-// attempt in attempt order, so the draw is that of one attempt at a time
+// attempt in attempt order, so the draw is that of one attempt at a time.  Not
+// inlined: one copy serves the Nc(Nc-1)/2 subgroups (instruction fetch)
 template <class R, int LANES, int PER>
-__device__ __forceinline__ bool heatbath_su2_group(R alpha, bool skip, uint2 key, uint32_t link, uint32_t step,
+__device__ __noinline__ bool heatbath_su2_group(R alpha, bool skip, uint2 key, uint32_t link, uint32_t step,
                                                    uint32_t sub, int q, int base, Quat<R>& b) {
   const bool kp = alpha >= R(1.5);
   const R inv2a = R(1) / (R(2) * alpha);

@@ -114,6 +114,39 @@ def test_fused_reunitarization_pass_is_elementwise(sunlib, nc, st, variant, dims
             assert link_diff(got, before).max() > 1e-5
 
 
+@pytest.mark.parametrize("dims", [SMALL, MEDIUM])
+@pytest.mark.parametrize("mode", [orc.OVERRELAX, orc.HEATBATH])
+def test_two_row_staple_fused_pass(sunlib, dims, mode):
+    """Variant 3 (register bound + two-row staple products, the headline's
+    kernels): the fused pass link by link on links on the group, where the
+    conj(row0 x row1) third row of each staple term is exact (1e-5); and on
+    links 1e-4 off the group, every updated link ends on the group."""
+    U = cold_thermal(3, dims, 6.0)
+    V = drifted(U, 1e-4, seed=3)
+    n_updates, flips = 0, 0
+    with sunlib.Lattice(3, dims, 6.0, seed=6, precision=32, storage=12, variant=3) as L:
+        for mu, par in PASSES:
+            L.import_links(U)
+            L.heatbath_step = 4
+            L.update_pass_reunit(mode, mu, par)
+            got = L.export_links()
+            orc.update_pass(U, 6.0, mode, mu, par, 4, 6, reunit_after=True)
+            d = link_diff(got, U)
+            if mode == orc.OVERRELAX:
+                assert d.max() < OR_TOL, (mu, par, float(d.max()))
+            else:
+                n_updates += d.size // 8
+                flips += check_heatbath(d, n_updates, (mu, par))
+            L.import_links(V)
+            L.update_pass_reunit(mode, mu, par)
+            moved = L.export_links().reshape(4, -1, 3, 3)
+            m = moved[mu].reshape(dims[3], dims[2], dims[1], dims[0], 3, 3)
+            t, z, y, x = np.meshgrid(*[np.arange(n) for n in (dims[3], dims[2], dims[1], dims[0])], indexing="ij")
+            updated = m[(x + y + z + t) % 2 == par]
+            assert unitarity(updated) < 2e-6
+            assert unitarity(V.reshape(4, -1, 3, 3)[mu]) > 1e-5
+
+
 @pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("dims", [SMALL, MEDIUM])
 def test_fused_step_reunitarizes_every_link(sunlib, dims, variant):
@@ -246,7 +279,7 @@ def test_full_size_headline_configuration(sunlib):
     6.2, cold start, six sweeps) tiled 3 x 3 x 3 x 3."""
     beta, seed = 6.2, 1
     tuned = sunlib.autotune(3, FULL, beta, 1, 5, precision=32, storage=12, reunit_mode=1, tune_storage=True,
-                            tune_reunit_mode=True)
+                            tune_reunit_mode=True, two_row=True)
     kw = dict(precision=32, storage=tuned["storage"], variant=tuned["variant"], reunit_mode=tuned["reunit_mode"],
               block_threads=tuned["block_threads"], graph_sweeps=tuned["graph_sweeps"])
     small = cold_thermal(3, TILE, beta)
@@ -273,9 +306,14 @@ def test_full_size_headline_configuration(sunlib):
         d = link_diff(got, want)
         assert d.max() < OR_TOL, float(d.max())
         del got, want, U
-        # the re-unitarizing step: one overrelaxation step with the tuned placement
+        # the re-unitarizing step: one overrelaxation step with the tuned placement;
+        # links off the group only where every link is re-unitarized before it is
+        # read and the staple products use all three rows of each term (with
+        # variant bit 2 a term's third row is conj(row0 x row1), exact on the group)
         mode = kw["reunit_mode"]
-        V = tiled(drifted(small, 1e-4, seed=5) if mode == 1 else small, REPS)
+        two_row_staple = (kw["variant"] & 2) != 0
+        off_group = mode == 1 and not two_row_staple
+        V = tiled(drifted(small, 1e-4, seed=5) if off_group else small, REPS)
         L.import_links(V)
         L.sweep(0, 1)
         got = L.export_links()
@@ -287,3 +325,10 @@ def test_full_size_headline_configuration(sunlib):
         # observables of the GPU's result against the oracle's on its own links
         assert abs(L.plaquette() - orc.plaquette(V)) < 2e-6
         assert abs(L.polyakov_loop() - orc.polyakov(V)) < 2e-5
+        del V
+        if mode == 1 and not off_group:
+            # every link of the step is re-unitarized: from links 1e-4 off the
+            # group the step ends on the group
+            L.import_links(tiled(drifted(small, 1e-4, seed=5), REPS))
+            L.sweep(0, 1)
+            assert unitarity(L.export_links()) < 2e-6
