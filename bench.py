@@ -861,7 +861,7 @@ def measure_batched(local, steps=3, tune=True, opts=None):
 
 
 def measure_serving(local, n_requests=80, budget_gb=64.0, policy="srpt", tick_ms=40.0, work_cap_ms=8.0,
-                    low_latency_cap_ms=3.0, sweeps_per_tick=None):
+                    low_latency_cap_ms=3.0, sweeps_per_tick=None, use_graphs=True):
     """C5: a Poisson request trace (mean 20/s, seed 7) of SU(Nc) chains, Nc in
     {2,3,4,6}, L in {8..24}, 20..200 sweeps each, served by continuous batching
     under a device-memory budget, with the server's per-Nc sweep costs measured
@@ -886,11 +886,16 @@ def measure_serving(local, n_requests=80, budget_gb=64.0, policy="srpt", tick_ms
     upd = sum(r.n_sweeps * 5 * 4 * r.L ** 4 for r in trace)
     stream = torch.cuda.current_stream()
 
-    def server(cap):
-        return lambda: serve.Server(budget, sweeps_per_tick=sweeps_per_tick, work_cap_ms=cap, tick_ms=tick_ms,
-                                    policy=policy, costs=costs).run(trace)
+    servers = {}
 
-    runs = [("served", server(work_cap_ms)), ("served_low_latency", server(low_latency_cap_ms)),
+    def server(cap, key):
+        def run():
+            servers[key] = serve.Server(budget, sweeps_per_tick=sweeps_per_tick, work_cap_ms=cap, tick_ms=tick_ms,
+                                        policy=policy, costs=costs, use_graphs=use_graphs)
+            return servers[key].run(trace)
+        return run
+
+    runs = [("served", server(work_cap_ms, "served")), ("served_low_latency", server(low_latency_cap_ms, "served_low_latency")),
             ("plain_fifo", lambda: serve.serve_plain(trace, order="fifo", costs=costs)[0]),
             ("plain_srpt", lambda: serve.serve_plain(trace, order="srpt", costs=costs)[0])]
     out = {}
@@ -903,6 +908,9 @@ def measure_serving(local, n_requests=80, budget_gb=64.0, policy="srpt", tick_ms
         out[name] = {"p50_s": st["p50_s"], "p99_s": st["p99_s"], "mean_s": st["mean_s"],
                      "completed": st["completed"], "wall_s": ms / 1e3, "requests_per_s": len(trace) / (ms / 1e3),
                      "link_updates_per_s": upd / (ms / 1e3), "clocks": clocks}
+        if name in servers:
+            out[name]["ticks"] = servers[name].ticks
+            out[name]["batches_built"] = servers[name].batches_built
     s, sl, pf, ps = out["served"], out["served_low_latency"], out["plain_fifo"], out["plain_srpt"]
     return {"metric": "requests/s", "value": s["requests_per_s"], "unit": "requests/s",
             "p50_s": s["p50_s"], "p99_s": s["p99_s"], "dtype": "f32",
@@ -943,7 +951,8 @@ def serving_arm(args):
     torch.cuda.set_device(0)
     r = measure_serving(0, n_requests=args.requests, budget_gb=args.budget_gb, policy=args.policy,
                         tick_ms=args.tick_ms, work_cap_ms=args.work_cap_ms,
-                        low_latency_cap_ms=args.low_latency_cap_ms, sweeps_per_tick=args.sweeps_per_tick or None)
+                        low_latency_cap_ms=args.low_latency_cap_ms, sweeps_per_tick=args.sweeps_per_tick or None,
+                        use_graphs=not args.serve_no_graphs)
     out = {"metric": "served requests/s", "value": r["value"], "unit": "requests/s", "n_gpus": 1, "steps": 1,
            "warmup": 1, "ms_per_step": r["served"]["wall_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic Poisson trace (seed 7)",
@@ -1006,6 +1015,8 @@ def main():
     ap.add_argument("--policy", choices=["srpt", "fifo"], default="srpt")
     ap.add_argument("--work-cap-ms", type=float, default=8.0,
                     help="serving: predicted ms of one batch sweep up to which chains are added to a tick")
+    ap.add_argument("--serve-no-graphs", action="store_true",
+                    help="serving: batches launch their kernels directly instead of capturing CUDA graphs")
     ap.add_argument("--low-latency-cap-ms", type=float, default=3.0,
                     help="serving: the same for the second, low-latency server setting")
     args = ap.parse_args()

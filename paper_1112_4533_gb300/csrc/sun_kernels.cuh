@@ -18,12 +18,14 @@ constexpr int kMaxBlockThreads = 256;
 // staple products (bit 2) the overrelaxation pass needs fewer registers and 6
 // blocks are faster (48^3 x 96: 0.533 -> 0.517 ms; its heatbath pass stays at 5)
 constexpr int kOccBlocks = 5;
-constexpr int kOccBlocksTwoRowOR = 6;
+constexpr int kOccBlocksTwoRowOR = 6;  // 7 and 8 blocks measured no faster
+constexpr int kOccBlocksTwoRowHB = 5;  // 6 blocks: 0.722 -> 0.767 ms
 // the same bound for the SU(4) FP32 per-link passes: 4 blocks (128 registers)
 constexpr int kOccBlocksSU4 = 4;
 template <int N, int VAR = 1, int MODE = 0>
 __host__ __device__ constexpr int occ_blocks() {
-  return N == 4 ? kOccBlocksSU4 : ((VAR & 2) != 0 && MODE == 1 ? kOccBlocksTwoRowOR : kOccBlocks);
+  return N == 4 ? kOccBlocksSU4
+                : ((VAR & 2) != 0 ? (MODE == 1 ? kOccBlocksTwoRowOR : kOccBlocksTwoRowHB) : kOccBlocks);
 }
 constexpr int kHeatbathMode = 0;
 constexpr int kOverrelaxMode = 1;

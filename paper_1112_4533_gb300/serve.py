@@ -137,6 +137,7 @@ class Server:
         self.clock = clock
         self.costs = costs  # ms per site of a sweep by Nc (None: the default table)
         self.ticks = 0
+        self.batches_built = 0
         self.link_updates = 0
 
     def _select(self, active):
@@ -185,6 +186,7 @@ class Server:
                 if batch is not None:
                     batch.close()
                 batch = sun.Batch([a[1] for a in sel], use_graphs=self.use_graphs)
+                self.batches_built += 1
                 members = ids
             k = min(a[0].n_sweeps - a[2] for a in sel)
             k = min(k, max(1, int(self.tick_ms / max(cost, 1e-6))))
