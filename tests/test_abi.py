@@ -93,6 +93,7 @@ def test_create_rejects_invalid_arguments_on_the_host(lib, nc, dims, prec, stora
 def test_calls_on_null_handles_fail_cleanly(lib):
     assert lib.sun_sweep(None, 1, 1) == 1
     assert lib.sun_update_pass(None, 0, 0, 0) == 1
+    assert lib.sun_update_pass_reunit(None, 0, 0, 0) == 1
     v = ctypes.c_double()
     assert lib.sun_plaquette(None, ctypes.byref(v)) == 1
     lib.sun_lattice_destroy(None)

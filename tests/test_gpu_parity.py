@@ -525,6 +525,8 @@ def test_invalid_pass_arguments_raise(sunlib):
         for args in [(2, 0, 0), (0, 4, 0), (0, 0, 2)]:
             with pytest.raises(sunlib.SunError):
                 L.update_pass(*args)
+            with pytest.raises(sunlib.SunError):
+                L.update_pass_reunit(*args)
         with pytest.raises(sunlib.SunError):
             L.heatbath_step = 2 ** 33
 
@@ -574,3 +576,11 @@ def test_su4_register_bound_equals_default_kernel(sunlib, reunit_mode):
                 out.append((L.export_links(), plaq, poly))
         assert np.array_equal(out[0][0], out[1][0]), dims
         assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][2], out[1][2])
+
+
+def test_fused_pass_unsupported_where_not_built(sunlib):
+    """FP64 passes of Nc >= 5 are built without the fused re-unitarization."""
+    with sunlib.Lattice(6, (4, 4, 4, 4), 25.2, precision=64) as L:
+        with pytest.raises(sunlib.SunError) as e:
+            L.update_pass_reunit(sunlib.OVERRELAX, 0, 0)
+        assert e.value.status == 5
