@@ -126,7 +126,7 @@ __device__ __forceinline__ void normalise_row(Mat<double, N>& m, int r) {
 }
 
 template <int N>
-__device__ __forceinline__ Cpx<double> det_lu(Mat<double, N> a) {
+__device__ __forceinline__ Cpx<double> det_lu_inplace(Mat<double, N>& a) {
   Cpx<double> det = {1.0, 0.0};
 #pragma unroll
   for (int c = 0; c < N; ++c) {
@@ -175,30 +175,40 @@ __device__ __forceinline__ Cpx<double> det_lu(Mat<double, N> a) {
 }
 
 template <int N>
+__device__ __forceinline__ Cpx<double> det_lu(Mat<double, N> a) {
+  return det_lu_inplace<N>(a);
+}
+
+// Gram-Schmidt of rows 0 .. ROWS-1 in order (Sec. 2)
+template <int N, int ROWS>
+__device__ __forceinline__ void gram_schmidt_rows(Mat<double, N>& m) {
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r) {
+#pragma unroll
+    for (int q = 0; q < r; ++q) {
+      Cpx<double> pr = {0.0, 0.0};
+#pragma unroll
+      for (int c = 0; c < N; ++c) ccfma(pr, m.e[q][c], m.e[r][c]);
+      // row r -= pr * row q
+#pragma unroll
+      for (int c = 0; c < N; ++c) {
+        const Cpx<double> a = m.e[q][c];
+        m.e[r][c].re = fma(pr.im, a.im, fma(-pr.re, a.re, m.e[r][c].re));
+        m.e[r][c].im = fma(-pr.im, a.re, fma(-pr.re, a.im, m.e[r][c].im));
+      }
+    }
+    normalise_row<N>(m, r);
+  }
+}
+
+template <int N>
 __device__ __forceinline__ void reunit_d(Mat<double, N>& m) {
   if constexpr (N == 2) {
     normalise_row<2>(m, 0);
     m.e[1][0] = {-m.e[0][1].re, m.e[0][1].im};
     m.e[1][1] = {m.e[0][0].re, -m.e[0][0].im};
   } else {
-    constexpr int rows = (N == 3) ? 2 : N;
-#pragma unroll
-    for (int r = 0; r < rows; ++r) {
-#pragma unroll
-      for (int q = 0; q < r; ++q) {
-        Cpx<double> pr = {0.0, 0.0};
-#pragma unroll
-        for (int c = 0; c < N; ++c) ccfma(pr, m.e[q][c], m.e[r][c]);
-        // row r -= pr * row q
-#pragma unroll
-        for (int c = 0; c < N; ++c) {
-          const Cpx<double> a = m.e[q][c];
-          m.e[r][c].re = fma(pr.im, a.im, fma(-pr.re, a.re, m.e[r][c].re));
-          m.e[r][c].im = fma(-pr.im, a.re, fma(-pr.re, a.im, m.e[r][c].im));
-        }
-      }
-      normalise_row<N>(m, r);
-    }
+    gram_schmidt_rows<N, (N == 3) ? 2 : N>(m);
     if constexpr (N == 3) {
       su3_third_row(m);
     } else {
@@ -1462,6 +1472,57 @@ __device__ __forceinline__ const char* obs_block(const ObsParams& p, int d, int 
   return p.links + (2 * d + par) * p.block_bytes;
 }
 
+// Entry e = k Nc + j of a full-storage link at half-site h of a block.
+template <class R, int N>
+__device__ __forceinline__ Cpx<R> load_entry(const char* blk, int64_t Vh, int64_t h, int e) {
+  if constexpr (sizeof(R) == 8) {  // one complex double per 16-byte component
+    const double2 v = __ldg(reinterpret_cast<const double2*>(blk + (int64_t(e) * Vh + h) * 16));
+    return {v.x, v.y};
+  } else {
+    constexpr int n16 = Layout<R, N, kFull>::n16;
+    const int cc = e >> 1;
+    const char* q = cc < n16 ? blk + (int64_t(cc) * Vh + h) * 16 + (e & 1) * 8 : blk + int64_t(n16) * Vh * 16 + h * 8;
+    const float2 v = __ldg(reinterpret_cast<const float2*>(q));
+    return {v.x, v.y};
+  }
+}
+
+// Re Tr((A B)(C D)^+) as retr_nd(mul_nn(A, B), mul_nn(C, D)) computes it, the
+// same operations in the same order, row by row: a row of A and of C at a time,
+// the entries of B and D read as they are used (from L1), so that no whole
+// Nc x Nc product is held (for Nc >= 5 the whole products do not fit in
+// registers and went to local memory).
+template <class R, int N>
+__device__ __forceinline__ R retr_products_by_rows(const char* a, int64_t ha, const char* b, int64_t hb, const char* c,
+                                                   int64_t hc, const char* d, int64_t hd, int64_t Vh) {
+  R s = R(0);
+#pragma unroll 1
+  for (int i = 0; i < N; ++i) {
+    Cpx<R> ar[N], cr[N], t1[N], t2[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      ar[k] = load_entry<R, N>(a, Vh, ha, i * N + k);
+      cr[k] = load_entry<R, N>(c, Vh, hc, i * N + k);
+    }
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      t1[j] = cmul(ar[0], load_entry<R, N>(b, Vh, hb, j));
+      t2[j] = cmul(cr[0], load_entry<R, N>(d, Vh, hd, j));
+#pragma unroll
+      for (int k = 1; k < N; ++k) {
+        cfma(t1[j], ar[k], load_entry<R, N>(b, Vh, hb, k * N + j));
+        cfma(t2[j], cr[k], load_entry<R, N>(d, Vh, hd, k * N + j));
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      s = fma(t1[j].re, t2[j].re, s);
+      s = fma(t1[j].im, t2[j].im, s);
+    }
+  }
+  return s;
+}
+
 // Sum over the six plaquettes P_{mu nu}(x) = U_mu(x) U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+
 // (Eq. 4) of one site (half-site h of parity par), ReTr in the storage
 // precision, each added in FP64.
@@ -1483,6 +1544,13 @@ __device__ __forceinline__ double site_plaquette(const ObsParams& p, int par, in
         const Quat<R> t1 = qmul(umx, load_quat<R>(obs_block(p, nu, par ^ 1), g.Vh, xpmu));
         const Quat<R> t2 = qmul(unx, load_quat<R>(obs_block(p, mu, par ^ 1), g.Vh, xpnu));
         acc += double(R(2) * (t1.a0 * t2.a0 + t1.a1 * t2.a1 + t1.a2 * t2.a2 + t1.a3 * t2.a3));
+      }
+    } else if constexpr (N >= 5) {
+#pragma unroll 1
+      for (int nu = mu + 1; nu < 4; ++nu) {
+        const int64_t xpnu = fwd(g, lex, s.c[nu], nu) >> 1;
+        acc += double(retr_products_by_rows<R, N>(obs_block(p, mu, par), h, obs_block(p, nu, par ^ 1), xpmu,
+                                                  obs_block(p, nu, par), h, obs_block(p, mu, par ^ 1), xpnu, g.Vh));
       }
     } else {
       const Mat<R, N> umx = load_mat<R, N, S>(obs_block(p, mu, par), g.Vh, h);
