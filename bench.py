@@ -795,7 +795,7 @@ def measure_batched(local, steps=3, tune=True, opts=None):
         t0 = time.perf_counter()
         tuned = sun.autotune_batch([(3, (L,) * 4, b) for L, b in zip(Ls, betas)], 1, 4, precision=32,
                                    storage=o["storage"], reunit_mode=o["reunit_mode"], tune_storage=True,
-                                   tune_reunit_mode=True)
+                                   tune_reunit_mode=True, two_row=True)
         tuned["tuning_s"] = time.perf_counter() - t0
         o.update({k: tuned[k] for k in ("storage", "variant", "reunit_mode", "block_threads")})
     kw = dict(precision=32, graph_sweeps=sweeps, **o)

@@ -91,6 +91,46 @@ def test_fp64_batch_matches_oracle(sunlib):
         L.close()
 
 
+# (nc, dims, beta, seed, storage, variant): FP32 chains of every kernel kind a
+# batch launches, the SU(3) one with the headline's variant (two-row staple products)
+MIX32 = [
+    (3, (8, 6, 4, 10), 6.0, 31, 12, 3),
+    (3, (4, 6, 4, 8), 6.0, 32, 12, 0),
+    (2, (8, 6, 4, 6), 2.3, 33, 4, 0),
+    (4, (4, 4, 6, 4), 11.2, 34, 32, 0),
+    (6, (4, 4, 4, 6), 25.2, 35, 72, 0),
+]
+
+
+@pytest.mark.parametrize("reunit_mode", [0, 1])
+def test_fp32_batch_matches_oracle(sunlib, reunit_mode):
+    """A mixed FP32 batch loaded with the oracle's thermalised configurations:
+    one sweep of one overrelaxation step (no accept/reject branch) and the
+    re-unitarization, every chain link by link against the oracle's sweep
+    (1e-5; the batched passes, row-parallel pass, re-unitarization and
+    plaquette kernels), and each chain's plaquette against the oracle's."""
+    from tests.oracle_configs import cold_thermal
+    specs = [sp for sp in MIX32 if reunit_mode == 0 or sp[0] <= 4]  # row-parallel SU(6): placement 0 only
+    lats, starts = [], []
+    for nc, dims, beta, seed, st, var in specs:
+        L = sunlib.Lattice(nc, dims, beta, seed=seed, storage=st, precision=32, variant=var,
+                           reunit_mode=reunit_mode)
+        U = cold_thermal(nc, dims, beta)
+        L.import_links(U)
+        lats.append(L)
+        starts.append(U)
+    with sunlib.Batch(lats) as B:
+        plaq, _ = B.run(1, 0, 1)
+    for i, (L, sp) in enumerate(zip(lats, specs)):
+        nc, dims, beta, seed = sp[:4]
+        want = starts[i].copy()
+        orc.sweep(want, beta, 0, 1, orc.REUNIT_FUSED if reunit_mode == 1 else True, seed, 0)
+        got = L.export_links()
+        assert np.abs(got - want).max() < 1e-5, (sp, float(np.abs(got - want).max()))
+        assert abs(plaq[0, i] - orc.plaquette(want)) < 2e-6, sp
+        L.close()
+
+
 def test_batch_argument_errors(sunlib):
     a = make(sunlib, MIX[0])
     b = make(sunlib, MIX[1], reunit_mode=1)
