@@ -411,6 +411,21 @@ sun_status sun_autotune_batch(int n, const int* nc, const int* dims, const doubl
 sun_status sun_plaquette_noalloc(const void* links, int nc, const int dims[4], int precision,
                                  int storage, double* out, void* stream);
 
+/* Self-test of the FP32 <-> FP64 conversions the kernels use (no counterpart in
+ * the paper; a diagnostic).  The re-unitarization kernels (sun_reunitarize)
+ * convert links between the FP32 storage and FP64 with integer operations on
+ * the IEEE 754 encodings, because GB300 runs its conversion instructions at its
+ * FP64 rate.  This compares them bit for bit with the
+ * hardware conversions on the current device: all 2^32 float encodings through
+ * float -> double, and n double encodings drawn from seed (exponents across and
+ * around the float's normal range, and rounding ties) through double -> float.
+ *  result[0]  float -> double mismatches     result[1]  double -> float mismatches
+ *  result[2]  smallest mismatching float encoding, result[3] smallest mismatching
+ *             double encoding (UINT64_MAX when there is none)
+ * Allocates 32 bytes of device memory for the call; uses the legacy default
+ * stream; syncs.  SUN_ERR_ARG if result is NULL, SUN_ERR_CUDA on a CUDA error. */
+sun_status sun_selftest_conversions(uint64_t n, uint64_t seed, uint64_t result[4]);
+
 #ifdef __cplusplus
 }
 #endif

@@ -7,6 +7,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "sun_runtime.h"
@@ -225,16 +226,92 @@ __device__ __forceinline__ R retr_nd(const Mat<R, N>& a, const Mat<R, N>& b) {
   return s;
 }
 
+// conj(a_k b_l - a_l b_k), entry (k, l) of conj(a x b), plus acc: each part is
+// one chain of fused multiply-adds started from acc
+template <class R>
+__device__ __forceinline__ Cpx<R> conj_cross_acc(Cpx<R> ak, Cpx<R> bl, Cpx<R> al, Cpx<R> bk, Cpx<R> acc) {
+  R re = fma(ak.re, bl.re, acc.re);
+  re = fma(-ak.im, bl.im, re);
+  re = fma(-al.re, bk.re, re);
+  re = fma(al.im, bk.im, re);
+  R im = fma(-ak.re, bl.im, acc.im);
+  im = fma(-ak.im, bl.re, im);
+  im = fma(al.re, bk.im, im);
+  im = fma(al.im, bk.re, im);
+  return {re, im};
+}
+
+// conj(a_k b_l - a_l b_k) alone: the chains start from the first product
+template <class R>
+__device__ __forceinline__ Cpx<R> conj_cross(Cpx<R> ak, Cpx<R> bl, Cpx<R> al, Cpx<R> bk) {
+  R re = ak.re * bl.re;
+  re = fma(-ak.im, bl.im, re);
+  re = fma(-al.re, bk.re, re);
+  re = fma(al.im, bk.im, re);
+  R im = -(ak.re * bl.im);
+  im = fma(-ak.im, bl.re, im);
+  im = fma(al.re, bk.im, im);
+  im = fma(al.im, bk.re, im);
+  return {re, im};
+}
+
 // row 2 of an SU(3) matrix from rows 0 and 1: conj(row0 x row1)
 template <class R>
 __device__ __forceinline__ void su3_third_row(Mat<R, 3>& m) {
   const Cpx<R>* a = m.e[0];
   const Cpx<R>* b = m.e[1];
-  Cpx<R> c0 = cmul(a[1], b[2]), c1 = cmul(a[2], b[0]), c2 = cmul(a[0], b[1]);
-  Cpx<R> d0 = cmul(a[2], b[1]), d1 = cmul(a[0], b[2]), d2 = cmul(a[1], b[0]);
-  m.e[2][0] = {c0.re - d0.re, -(c0.im - d0.im)};
-  m.e[2][1] = {c1.re - d1.re, -(c1.im - d1.im)};
-  m.e[2][2] = {c2.re - d2.re, -(c2.im - d2.im)};
+  m.e[2][0] = conj_cross(a[1], b[2], a[2], b[1]);
+  m.e[2][1] = conj_cross(a[2], b[0], a[0], b[2]);
+  m.e[2][2] = conj_cross(a[0], b[1], a[1], b[0]);
+}
+
+// ------------------------------------------- FP32 <-> FP64 conversions ----
+// GB300 converts between FP32 and FP64 at its FP64 rate: about 2 conversions a
+// clock per SM, the rate of its FP64 FMAs, against about 118 FP32 FMAs
+// (measured).  to_f64 and to_f32 do these conversions with integer operations on
+// the IEEE 754 binary32 and binary64 encodings (sign, biased exponent, fraction):
+// float -> double is exact (the fraction is extended by 29 zero bits and the
+// exponent rebiased from 127 to 1023); double -> float keeps the top 23 fraction
+// bits and rounds to nearest, ties to even, on the 29 bits dropped.  Operands the
+// integer path does not cover (subnormal, infinite or NaN floats; doubles whose
+// float is subnormal, infinite or NaN) take the hardware conversion, so both
+// functions return exactly the hardware's result for every operand
+// (sun_selftest_conversions checks this bit for bit).
+__device__ __forceinline__ double to_f64(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t e = (b >> 23) & 0xffu;
+  if (e == 0xffu || (e == 0u && (b << 9) != 0u)) return double(f);
+  const uint32_t ed = e == 0u ? 0u : e + 896u;  // +-0 keeps exponent 0
+  const uint32_t hi = (b & 0x80000000u) | (ed << 20) | ((b >> 3) & 0x000fffffu);
+  return __hiloint2double(int(hi), int(b << 29));
+}
+__device__ __forceinline__ double to_f64(double d) { return d; }
+
+__device__ __forceinline__ float to_f32(double d) {
+  const uint32_t hi = uint32_t(__double2hiint(d)), lo = uint32_t(__double2loint(d));
+  const uint32_t e = (hi >> 20) & 0x7ffu;
+  if (e - 897u < 254u) {  // the float is normal before rounding: exponent e - 896 in [1, 254]
+    uint32_t f = (hi & 0x80000000u) | ((e - 896u) << 23) | ((hi & 0x000fffffu) << 3) | (lo >> 29);
+    const uint32_t rest = lo & 0x1fffffffu;
+    // a carry out of the fraction raises the exponent (254 -> 255 is the overflow to infinity)
+    f += (rest > 0x10000000u || (rest == 0x10000000u && (f & 1u) != 0u)) ? 1u : 0u;
+    return __uint_as_float(f);
+  }
+  if (((hi << 1) | lo) == 0u) return __uint_as_float(hi & 0x80000000u);  // +-0
+  return float(d);
+}
+__device__ __forceinline__ float to_f32(float f) { return f; }
+
+// conversion between the storage and the FP64 working precision
+template <class B>
+__device__ __forceinline__ B convert_to(float x) {
+  if constexpr (std::is_same<B, double>::value) return to_f64(x);
+  else return B(x);
+}
+template <class B>
+__device__ __forceinline__ B convert_to(double x) {
+  if constexpr (std::is_same<B, float>::value) return to_f32(x);
+  else return B(x);
 }
 
 // ------------------------------------------------------------ quaternions ----

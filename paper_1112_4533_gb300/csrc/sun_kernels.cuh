@@ -231,6 +231,22 @@ __device__ __forceinline__ Mat<B, N> mat_cast(const Mat<A, N>& m) {
   return o;
 }
 
+// mat_cast with the FP32 <-> FP64 conversions done on the integer pipe (to_f64,
+// to_f32: the same bits).  For the re-unitarization kernels, whose time is the
+// FP64 pipe's (measured, separate pass: SU(4) 32^4 4.19 -> 3.92 ms, SU(6) 24^4
+// 4.05 -> 3.92 ms).  Not in the update passes: there the hardware conversions
+// overlap the FP32 work, and the integer sequences cost issue slots (the fused
+// re-unitarizing step 6.46 -> 6.77 ms, the plaquette 0.75 -> 0.81 ms).
+template <class A, class B, int N>
+__device__ __forceinline__ Mat<B, N> mat_cast_int(const Mat<A, N>& m) {
+  Mat<B, N> o;
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = 0; j < N; ++j) o.e[i][j] = {convert_to<B>(m.e[i][j].re), convert_to<B>(m.e[i][j].im)};
+  return o;
+}
+
 // ---------------------------------------------------------------------------
 // Staple terms (Eq. 9).  With ROWS2 (SU(3) two-row storage, kernel variant bit
 // 1) only rows 0 and 1 of each term are multiplied out and the term's third row
@@ -254,6 +270,22 @@ __device__ __forceinline__ Rows2<R> load_rows2(const char* blk, int64_t Vh, int6
   return m;
 }
 
+// st += the SU(3) term with rows t[0], t[1] and third row conj(t0 x t1): rows 0
+// and 1 added, the third row's entries accumulated into st by fused chains
+template <class R>
+__device__ __forceinline__ void add_two_row_term(Mat<R, 3>& st, const Cpx<R> (&t)[2][3]) {
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      st.e[i][j].re += t[i][j].re;
+      st.e[i][j].im += t[i][j].im;
+    }
+  st.e[2][0] = conj_cross_acc(t[0][1], t[1][2], t[0][2], t[1][1], st.e[2][0]);
+  st.e[2][1] = conj_cross_acc(t[0][2], t[1][0], t[0][0], t[1][2], st.e[2][1]);
+  st.e[2][2] = conj_cross_acc(t[0][0], t[1][1], t[0][1], t[1][0], st.e[2][2]);
+}
+
 // U_nu(x) U_mu(x+nu) U_nu(x+mu)^+ added to st; BL: how U_mu is loaded
 template <class R, int N, int S, bool ROWS2, int BL>
 __device__ __forceinline__ void staple_forward(Mat<R, N>& st, const char* pa, int64_t ha, const char* pb, int64_t hb,
@@ -272,7 +304,7 @@ __device__ __forceinline__ void staple_forward(Mat<R, N>& st, const char* pa, in
         ab[i][j] = x;
       }
     const Mat<R, 3> c = load_mat<R, 3, S>(pc, Vh, hc);
-    Mat<R, 3> t;
+    Cpx<R> t[2][3];
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
@@ -280,16 +312,9 @@ __device__ __forceinline__ void staple_forward(Mat<R, N>& st, const char* pa, in
         Cpx<R> x = cmulc(ab[i][0], c.e[j][0]);
         cfmac(x, ab[i][1], c.e[j][1]);
         cfmac(x, ab[i][2], c.e[j][2]);
-        t.e[i][j] = x;
+        t[i][j] = x;
       }
-    su3_third_row(t);
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        st.e[i][j].re += t.e[i][j].re;
-        st.e[i][j].im += t.e[i][j].im;
-      }
+    add_two_row_term(st, t);
   } else {
     const Mat<R, N> a = load_mat<R, N, S>(pa, Vh, ha);
     const Mat<R, N> b = load_mat<R, N, S, BL>(pb, Vh, hb);
@@ -306,13 +331,8 @@ __device__ __forceinline__ void staple_backward(Mat<R, N>& st, const char* pa, i
   if constexpr (S == kTwoRow && ROWS2) {
     const Rows2<R> a = load_rows2<R>(pa, Vh, ha);
     // entries (2,0), (2,1) of the third row conj(row0 x row1) of a
-    Cpx<R> a20, a21;
-    {
-      const Cpx<R> p = cmul(a.e[0][1], a.e[1][2]), q = cmul(a.e[0][2], a.e[1][1]);
-      a20 = {p.re - q.re, -(p.im - q.im)};
-      const Cpx<R> u = cmul(a.e[0][2], a.e[1][0]), v = cmul(a.e[0][0], a.e[1][2]);
-      a21 = {u.re - v.re, -(u.im - v.im)};
-    }
+    const Cpx<R> a20 = conj_cross(a.e[0][1], a.e[1][2], a.e[0][2], a.e[1][1]);
+    const Cpx<R> a21 = conj_cross(a.e[0][2], a.e[1][0], a.e[0][0], a.e[1][2]);
     const Mat<R, 3> b = load_mat<R, 3, S, BL>(pb, Vh, hb);
     // rows 0,1 of a^+ b: (a^+ b)_ik = sum_m conj(a_mi) b_mk
     Cpx<R> d[2][3];
@@ -328,7 +348,7 @@ __device__ __forceinline__ void staple_backward(Mat<R, N>& st, const char* pa, i
       d[1][k] = y;
     }
     const Mat<R, 3> c = load_mat<R, 3, S>(pc, Vh, hc);
-    Mat<R, 3> t;
+    Cpx<R> t[2][3];
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
@@ -336,16 +356,9 @@ __device__ __forceinline__ void staple_backward(Mat<R, N>& st, const char* pa, i
         Cpx<R> x = cmul(d[i][0], c.e[0][j]);
         cfma(x, d[i][1], c.e[1][j]);
         cfma(x, d[i][2], c.e[2][j]);
-        t.e[i][j] = x;
+        t[i][j] = x;
       }
-    su3_third_row(t);
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        st.e[i][j].re += t.e[i][j].re;
-        st.e[i][j].im += t.e[i][j].im;
-      }
+    add_two_row_term(st, t);
   } else {
     const Mat<R, N> a = load_mat<R, N, S>(pa, Vh, ha);
     const Mat<R, N> b = load_mat<R, N, S, BL>(pb, Vh, hb);
@@ -1354,9 +1367,9 @@ __global__ void __launch_bounds__(256) reunit_kernel(const LinkParams p) {
     const double inv = rsqrt_near_one(fma(a1, a1, fma(a2, a2, fma(a3, a3, a0 * a0))));
     store_quat<R>(blk, p.g.Vh, h, Quat<R>{R(a0 * inv), R(a1 * inv), R(a2 * inv), R(a3 * inv)});
   } else {
-    Mat<double, N> m = mat_cast<R, double, N>(load_mat<R, N, S, kLoadPlain>(blk, p.g.Vh, h));
+    Mat<double, N> m = mat_cast_int<R, double, N>(load_mat<R, N, S, kLoadPlain>(blk, p.g.Vh, h));
     reunit_d<N>(m);
-    store_mat<R, N, S>(blk, p.g.Vh, h, mat_cast<double, R, N>(m));
+    store_mat<R, N, S>(blk, p.g.Vh, h, mat_cast_int<double, R, N>(m));
   }
 }
 
@@ -1523,15 +1536,68 @@ __device__ __forceinline__ R retr_products_by_rows(const char* a, int64_t ha, co
   return s;
 }
 
+// Re Tr(X Y^+) of two SU(3) matrices given by rows 0 and 1 (row 2 of each is
+// conj(row0 x row1)).  With d_ab = sum_j X_aj conj(Y_bj), rows 0 and 1 give
+// Re(d00 + d11), and row 2 gives Re conj(d00 d11 - d01 d10) by the identity
+// (a x b).(c x d) = (a.c)(b.d) - (a.d)(b.c) for the cross products of rows.
+template <class R>
+__device__ __forceinline__ R retr_nd_two_row(const Cpx<R> (&x)[2][3], const Cpx<R> (&y)[2][3]) {
+  Cpx<R> d[2][2];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      d[a][b] = cmulc(x[a][0], y[b][0]);
+#pragma unroll
+      for (int j = 1; j < 3; ++j) cfmac(d[a][b], x[a][j], y[b][j]);
+    }
+  R t = fma(d[0][0].re, d[1][1].re, -(d[0][0].im * d[1][1].im));
+  t = fma(-d[0][1].re, d[1][0].re, t);
+  t = fma(d[0][1].im, d[1][0].im, t);
+  return d[0][0].re + d[1][1].re + t;
+}
+
+// Rows 0 and 1 of A B
+template <class R>
+__device__ __forceinline__ void mul_nn_two_rows(const Mat<R, 3>& a, const Mat<R, 3>& b, Cpx<R> (&c)[2][3]) {
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      Cpx<R> s = cmul(a.e[i][0], b.e[0][j]);
+      cfma(s, a.e[i][1], b.e[1][j]);
+      cfma(s, a.e[i][2], b.e[2][j]);
+      c[i][j] = s;
+    }
+}
+
 // Sum over the six plaquettes P_{mu nu}(x) = U_mu(x) U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+
 // (Eq. 4) of one site (half-site h of parity par), ReTr in the storage
-// precision, each added in FP64.
+// precision, each added in FP64.  SU(3) two-row links: each ReTr from rows 0 and
+// 1 of the two products (retr_nd_two_row).
 template <class R, int N, int S>
 __device__ __forceinline__ double site_plaquette(const ObsParams& p, int par, int64_t h) {
   const Geom& g = p.g;
   const Site s = decode_half(g, h, par);
   const uint32_t lex = uint32_t(s.lex);
   double acc = 0.0;
+  if constexpr (S == kTwoRow) {
+#pragma unroll
+    for (int mu = 0; mu < 3; ++mu) {
+      const int64_t xpmu = fwd(g, lex, s.c[mu], mu) >> 1;
+      const Mat<R, 3> umx = load_mat<R, 3, S>(obs_block(p, mu, par), g.Vh, h);
+#pragma unroll
+      for (int nu = mu + 1; nu < 4; ++nu) {
+        const int64_t xpnu = fwd(g, lex, s.c[nu], nu) >> 1;
+        Cpx<R> t1[2][3], t2[2][3];
+        mul_nn_two_rows(umx, load_mat<R, 3, S>(obs_block(p, nu, par ^ 1), g.Vh, xpmu), t1);
+        mul_nn_two_rows(load_mat<R, 3, S>(obs_block(p, nu, par), g.Vh, h),
+                        load_mat<R, 3, S>(obs_block(p, mu, par ^ 1), g.Vh, xpnu), t2);
+        acc += double(retr_nd_two_row(t1, t2));
+      }
+    }
+    return acc;
+  }
 #pragma unroll
   for (int mu = 0; mu < 3; ++mu) {
     const int64_t xpmu = fwd(g, lex, s.c[mu], mu) >> 1;
@@ -1892,9 +1958,9 @@ __global__ void __launch_bounds__(128) reunit_batch(const BatchParams bp) {
     const double inv = rsqrt_near_one(fma(a1, a1, fma(a2, a2, fma(a3, a3, a0 * a0))));
     store_quat<R>(blk, sp.g.Vh, h, Quat<R>{R(a0 * inv), R(a1 * inv), R(a2 * inv), R(a3 * inv)});
   } else {
-    Mat<double, N> m = mat_cast<R, double, N>(load_mat<R, N, S, kLoadPlain>(blk, sp.g.Vh, h));
+    Mat<double, N> m = mat_cast_int<R, double, N>(load_mat<R, N, S, kLoadPlain>(blk, sp.g.Vh, h));
     reunit_d<N>(m);
-    store_mat<R, N, S>(blk, sp.g.Vh, h, mat_cast<double, R, N>(m));
+    store_mat<R, N, S>(blk, sp.g.Vh, h, mat_cast_int<double, R, N>(m));
   }
 }
 

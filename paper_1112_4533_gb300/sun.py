@@ -79,6 +79,7 @@ SIGNATURES = [
     ("sun_synchronize", ctypes.c_int, [_P]),
     ("sun_get_info", ctypes.c_int, [_P, ctypes.POINTER(LatticeInfo)]),
     ("sun_plaquette_noalloc", ctypes.c_int, [_P, ctypes.c_int, _I4, ctypes.c_int, ctypes.c_int, _D, _P]),
+    ("sun_selftest_conversions", ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]),
     ("sun_batch_create", ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int, _P, ctypes.c_int]),
     ("sun_batch_run", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D]),
     ("sun_batch_destroy", None, [_P]),

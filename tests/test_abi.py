@@ -96,6 +96,7 @@ def test_calls_on_null_handles_fail_cleanly(lib):
     assert lib.sun_update_pass_reunit(None, 0, 0, 0) == 1
     v = ctypes.c_double()
     assert lib.sun_plaquette(None, ctypes.byref(v)) == 1
+    assert lib.sun_selftest_conversions(16, 1, None) == 1
     lib.sun_lattice_destroy(None)
 
 
