@@ -196,8 +196,10 @@ sun_status sun_polyakov_loop(sun_lattice* lat, double* re, double* im);
  * 8*Nc*Nc*V; the buffer 16-byte aligned).  Export rebuilds the third row of
  * 12-real storage; import of a 12-real lattice keeps rows 0 and 1 only.
  * Page-locked host memory is read or written directly by the conversion kernel
- * (mapped into the device address space); pageable memory goes through a
- * device staging buffer in chunks.  Both sync. */
+ * (mapped into the device address space).  Pageable memory is read directly too
+ * where the device reaches it through the host's page tables (a Grace host on
+ * NVLink-C2C); otherwise, and for every export to pageable memory, it goes
+ * through a device staging buffer in chunks.  Both sync. */
 sun_status sun_export_links(sun_lattice* lat, double* host, size_t n_doubles);
 sun_status sun_import_links(sun_lattice* lat, const double* host, size_t n_doubles);
 
@@ -215,8 +217,9 @@ sun_status sun_check_links(sun_lattice* lat, double* max_unitarity_dev, double* 
  * bytes (sun_lattice_info.links_bytes).  Exact both ways: the stored values
  * themselves.  SU(2) quaternion storage: row 0 = (a0 + i a3, a2 + i a1).  The
  * buffer must be 16-byte aligned; page-locked host memory is read or written
- * directly by the conversion kernel, pageable memory goes through the staging
- * buffer.  Both sync. */
+ * directly by the conversion kernel, and pageable memory as for
+ * sun_import_links / sun_export_links (read in place where the device can,
+ * written through the staging buffer).  Both sync. */
 sun_status sun_export_stored(sun_lattice* lat, void* host, size_t bytes);
 sun_status sun_import_stored(sun_lattice* lat, const void* host, size_t bytes);
 

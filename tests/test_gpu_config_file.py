@@ -84,7 +84,10 @@ def test_damaged_file_leaves_the_lattice_unchanged(sunlib, tmp_path):
 @pytest.mark.parametrize("nc,st,prec", CASES)
 def test_compact_host_format(sunlib, nc, st, prec):
     """sun_export_stored: the stored rows of the canonical export in the storage
-    precision; pinned and pageable buffers agree; the round trip is exact."""
+    precision; pinned and pageable buffers agree, in both formats (pinned memory
+    is read and written in place, pageable memory read in place where the device
+    reaches it through the host's page tables and written through the staging
+    buffer); the round trips are exact."""
     import torch
     dims = (4, 4, 4, 6)
     rows = st // (2 * nc)
@@ -104,6 +107,15 @@ def test_compact_host_format(sunlib, nc, st, prec):
         assert np.array_equal(L.export_links(), U)
         L.run(1, 1, 1)
         L.import_stored_raw(pinned.data_ptr(), raw.nbytes)
+        assert np.array_equal(L.export_links(), U)
+        canon = torch.empty(U.nbytes, dtype=torch.uint8).pin_memory()
+        L.export_links_raw(canon.data_ptr(), 2 * U.size)
+        assert np.array_equal(canon.numpy().view(np.complex128).reshape(U.shape), U)
+        L.run(1, 1, 1)
+        L.import_links_raw(canon.data_ptr(), 2 * U.size)
+        assert np.array_equal(L.export_links(), U)
+        L.run(1, 1, 1)
+        L.import_links(U)
         assert np.array_equal(L.export_links(), U)
 
 
