@@ -342,6 +342,19 @@ __device__ __forceinline__ Quat<R> qadd(Quat<R> p, Quat<R> q) {
   return {p.a0 + q.a0, p.a1 + q.a1, p.a2 + q.a2, p.a3 + q.a3};
 }
 
+// Overrelaxation element of one subgroup (Eq. 17), A = (vhat^+)^2, from v = c vhat
+// (any c > 0) with n3 = |v_vec|^2 and k2 = v0^2 + n3.  A quaternion q = (q0, q)
+// squares to (q0^2 - |q|^2, 2 q0 q), so with v^+ = (v0, -v_vec)
+//   A = ((v0^2 - n3) / k2, -2 v0 v_vec / k2):
+// no square root and one division; the scale c cancels, and a power-of-two c
+// gives bitwise the same A.
+template <class R>
+__device__ __forceinline__ Quat<R> or_element(const Quat<R>& v, R n3, R k2) {
+  const R inv = R(1) / k2;
+  const R c = -(v.a0 + v.a0) * inv;
+  return {fma(v.a0, v.a0, -n3) * inv, c * v.a1, c * v.a2, c * v.a3};
+}
+
 // projection of a 2x2 block [[w00, w01], [w10, w11]] onto the real span of SU(2)
 template <class R>
 __device__ __forceinline__ Quat<R> block_to_quat(Cpx<R> w00, Cpx<R> w01, Cpx<R> w10, Cpx<R> w11) {
@@ -351,6 +364,11 @@ __device__ __forceinline__ Quat<R> block_to_quat(Cpx<R> w00, Cpx<R> w01, Cpx<R> 
   v.a1 = R(0.5) * (w01.im + w10.im);
   v.a2 = R(0.5) * (w01.re - w10.re);
   return v;
+}
+// twice that projection (exactly: no factor 1/2), for or_element
+template <class R>
+__device__ __forceinline__ Quat<R> block_to_quat2(Cpx<R> w00, Cpx<R> w01, Cpx<R> w10, Cpx<R> w11) {
+  return {w00.re + w11.re, w01.im + w10.im, w01.re - w10.re, w00.im - w11.im};
 }
 
 // ---------------------------------------------------------------- Philox ----

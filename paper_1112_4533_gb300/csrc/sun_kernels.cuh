@@ -422,21 +422,27 @@ __device__ __forceinline__ void pass_body(const PassParams& p, int par, int64_t 
 #pragma unroll
     for (int j = i + 1; j < N; ++j) {
       const bool last = (i == N - 2) && (j == N - 1);
-      const Quat<R> v = block_to_quat(w.e[i][i], w.e[i][j], w.e[j][i], w.e[j][j]);
-      const R k = d_sqrt(fma(v.a0, v.a0, fma(v.a1, v.a1, fma(v.a2, v.a2, v.a3 * v.a3))));
-      if (k > R(1e-15) && d_isfinite(k)) {
-        const R inv = R(1) / k;
-        const Quat<R> vd = {v.a0 * inv, -v.a1 * inv, -v.a2 * inv, -v.a3 * inv};  // vhat^+
-        Quat<R> a;
-        bool apply = true;
-        if constexpr (MODE == kHeatbathMode) {
+      if constexpr (MODE == kHeatbathMode) {
+        const Quat<R> v = block_to_quat(w.e[i][i], w.e[i][j], w.e[j][i], w.e[j][j]);
+        const R k = d_sqrt(fma(v.a0, v.a0, fma(v.a1, v.a1, fma(v.a2, v.a2, v.a3 * v.a3))));
+        if (k > R(1e-15) && d_isfinite(k)) {
+          const R inv = R(1) / k;
+          const Quat<R> vd = {v.a0 * inv, -v.a1 * inv, -v.a2 * inv, -v.a3 * inv};  // vhat^+
           Quat<R> b;
-          apply = heatbath_su2<R>(alpha_coef * k, p.key, link_id, step, uint32_t(sub), b);
-          a = qmul(b, vd);
-        } else {
-          a = qmul(vd, vd);
+          const bool apply = heatbath_su2<R>(alpha_coef * k, p.key, link_id, step, uint32_t(sub), b);
+          const Quat<R> a = qmul(b, vd);
+          if (apply) {
+            apply_rows(u, i, j, a);
+            if (!last) apply_rows(w, i, j, a);
+          }
         }
-        if (apply) {
+      } else {
+        // v2 = 2v: |v2|^2 = 4 k^2, compared with 4 (1e-15)^2
+        const Quat<R> v2 = block_to_quat2(w.e[i][i], w.e[i][j], w.e[j][i], w.e[j][j]);
+        const R n3 = fma(v2.a1, v2.a1, fma(v2.a2, v2.a2, v2.a3 * v2.a3));
+        const R k2 = fma(v2.a0, v2.a0, n3);
+        if (k2 > R(4e-30) && d_isfinite(k2)) {
+          const Quat<R> a = or_element(v2, n3, k2);
           apply_rows(u, i, j, a);
           if (!last) apply_rows(w, i, j, a);
         }
@@ -911,21 +917,26 @@ __device__ __forceinline__ void group_pass_body(const PassParams& p, int64_t fir
       const Cpx<R> wji = {__shfl_sync(0xffffffffu, wc[i % RB][jn].re, li), __shfl_sync(0xffffffffu, wc[i % RB][jn].im, li)};
       const Cpx<R> wij = {__shfl_sync(0xffffffffu, wc[jn % RB][i].re, lj), __shfl_sync(0xffffffffu, wc[jn % RB][i].im, lj)};
       const Cpx<R> wjj = {__shfl_sync(0xffffffffu, wc[jn % RB][jn].re, lj), __shfl_sync(0xffffffffu, wc[jn % RB][jn].im, lj)};
-      const Quat<R> v = block_to_quat(wii, wij, wji, wjj);
-      const R k = d_sqrt(fma(v.a0, v.a0, fma(v.a1, v.a1, fma(v.a2, v.a2, v.a3 * v.a3))));
-      const bool ok = active && k > R(1e-15) && d_isfinite(k);
-      const R inv = ok ? R(1) / k : R(0);
-      const Quat<R> vd = {v.a0 * inv, -v.a1 * inv, -v.a2 * inv, -v.a3 * inv};
       Quat<R> a;
-      bool apply = ok;
+      bool apply;
       if constexpr (MODE == kHeatbathMode) {
+        const Quat<R> v = block_to_quat(wii, wij, wji, wjj);
+        const R k = d_sqrt(fma(v.a0, v.a0, fma(v.a1, v.a1, fma(v.a2, v.a2, v.a3 * v.a3))));
+        const bool ok = active && k > R(1e-15) && d_isfinite(k);
+        const R inv = ok ? R(1) / k : R(0);
+        const Quat<R> vd = {v.a0 * inv, -v.a1 * inv, -v.a2 * inv, -v.a3 * inv};
         Quat<R> b;
         const bool drawn = heatbath_su2_group<R, LPL, RB>(ok ? alpha_coef * k : R(1), !ok, p.key, link_id, step,
                                                           uint32_t(sub), q, base, b);
         apply = ok && drawn;
         a = qmul(b, vd);
       } else {
-        a = qmul(vd, vd);
+        // v2 = 2v, as in the one-thread-per-link pass
+        const Quat<R> v2 = block_to_quat2(wii, wij, wji, wjj);
+        const R n3 = fma(v2.a1, v2.a1, fma(v2.a2, v2.a2, v2.a3 * v2.a3));
+        const R k2 = fma(v2.a0, v2.a0, n3);
+        apply = active && k2 > R(4e-30) && d_isfinite(k2);
+        a = or_element(v2, n3, apply ? k2 : R(1));
       }
       if (apply) {
         const Cpx<R> A00 = {a.a0, a.a3}, A01 = {a.a2, a.a1}, A10 = {-a.a2, a.a1}, A11 = {a.a0, -a.a3};
@@ -1037,18 +1048,20 @@ __device__ __forceinline__ void quat_pass_body(const PassParams& p, int par, int
   char* ublk = p.links + (2 * mu + par) * p.block_bytes;
   Quat<R> u = load_quat<R, kLoadPlain>(ublk, g.Vh, h);
   const Quat<R> w = qmul(u, qdag(st));
-  const R k = d_sqrt(fma(w.a0, w.a0, fma(w.a1, w.a1, fma(w.a2, w.a2, w.a3 * w.a3))));
-  if (k > R(1e-15) && d_isfinite(k)) {
-    const R inv = R(1) / k;
-    const Quat<R> vd = {w.a0 * inv, -w.a1 * inv, -w.a2 * inv, -w.a3 * inv};
-    if constexpr (MODE == kHeatbathMode) {
+  if constexpr (MODE == kHeatbathMode) {
+    const R k = d_sqrt(fma(w.a0, w.a0, fma(w.a1, w.a1, fma(w.a2, w.a2, w.a3 * w.a3))));
+    if (k > R(1e-15) && d_isfinite(k)) {
+      const R inv = R(1) / k;
+      const Quat<R> vd = {w.a0 * inv, -w.a1 * inv, -w.a2 * inv, -w.a3 * inv};
       const uint32_t step = *p.hb_step + p.step_offset;
       const uint32_t link_id = uint32_t(mu) * p.v_global + global_lex(p, lex);
       Quat<R> b;
       if (heatbath_su2<R>(R(p.alpha_coef) * k, p.key, link_id, step, 0u, b)) u = qmul(qmul(b, vd), u);
-    } else {
-      u = qmul(qmul(vd, vd), u);
     }
+  } else {
+    const R n3 = fma(w.a1, w.a1, fma(w.a2, w.a2, w.a3 * w.a3));
+    const R k2 = fma(w.a0, w.a0, n3);
+    if (k2 > R(1e-30) && d_isfinite(k2)) u = qmul(or_element(w, n3, k2), u);
   }
   if constexpr (REUNIT) {
     if (reunit_selected(p, global_lex(p, lex) >> 1)) {
@@ -1293,15 +1306,15 @@ __device__ __forceinline__ void or_pass_body2(const PassParams& p, int par, int6
 #pragma unroll
     for (int j = i + 1; j < N; ++j) {
       const bool last = (i == N - 2) && (j == N - 1);
-      const Quat<F2> v = block_to_quat(w.e[i][i], w.e[i][j], w.e[j][i], w.e[j][j]);
+      // or_element of each lane, operation by operation (v2 = 2v)
+      const Quat<F2> v2 = block_to_quat2(w.e[i][i], w.e[i][j], w.e[j][i], w.e[j][j]);
+      const F2 n3 = fma(v2.a1, v2.a1, fma(v2.a2, v2.a2, v2.a3 * v2.a3));
       float k0, k1;
-      f2_unpack(fma(v.a0, v.a0, fma(v.a1, v.a1, fma(v.a2, v.a2, v.a3 * v.a3))), k0, k1);
-      k0 = sqrtf(k0);
-      k1 = sqrtf(k1);
-      const bool ok0 = k0 > 1e-15f && isfinite(k0), ok1 = k1 > 1e-15f && isfinite(k1);
+      f2_unpack(fma(v2.a0, v2.a0, n3), k0, k1);
+      const bool ok0 = k0 > 4e-30f && isfinite(k0), ok1 = k1 > 4e-30f && isfinite(k1);
       const F2 inv = f2_pack(ok0 ? 1.0f / k0 : 0.0f, ok1 ? 1.0f / k1 : 0.0f);
-      const Quat<F2> vd = {v.a0 * inv, -v.a1 * inv, -v.a2 * inv, -v.a3 * inv};  // vhat^+
-      Quat<F2> a = qmul(vd, vd);
+      const F2 c = -(v2.a0 + v2.a0) * inv;
+      Quat<F2> a = {fma(v2.a0, v2.a0, -n3) * inv, c * v2.a1, c * v2.a2, c * v2.a3};
       if (!(ok0 && ok1)) {
         // a skipped subgroup of one lane: the identity there (applies exactly)
         float x0, x1;
