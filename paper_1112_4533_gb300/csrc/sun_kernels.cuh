@@ -368,6 +368,21 @@ __device__ __forceinline__ void staple_backward(Mat<R, N>& st, const char* pa, i
   }
 }
 
+// (U St^+)_ab = sum_k U_ak conj(St_bk)
+template <class R, int N>
+__device__ __forceinline__ Cpx<R> row_dot_c(const Mat<R, N>& u, int a, const Mat<R, N>& st, int b) {
+  Cpx<R> x = cmulc(u.e[a][0], st.e[b][0]);
+#pragma unroll
+  for (int k = 1; k < N; ++k) cfmac(x, u.e[a][k], st.e[b][k]);
+  return x;
+}
+// twice the SU(2) projection of the (i,j) block of W = U St^+, from the current U
+template <class R, int N>
+__device__ __forceinline__ Quat<R> or_block(const Mat<R, N>& u, const Mat<R, N>& st, int i, int j) {
+  return block_to_quat2(row_dot_c<R, N>(u, i, st, i), row_dot_c<R, N>(u, i, st, j), row_dot_c<R, N>(u, j, st, i),
+                        row_dot_c<R, N>(u, j, st, j));
+}
+
 // ---------------------------------------------------------------------------
 // One chessboard pass over matrices (Nc >= 2, full or two-row storage):
 // staple (Eq. 9) -> W = U Sigma^+ -> SU(2) subgroups in lexicographic order
@@ -408,7 +423,12 @@ __device__ __forceinline__ void pass_body(const PassParams& p, int par, int64_t 
 
   char* ublk = p.links + (2 * mu + par) * p.block_bytes;
   Mat<R, N> u = load_mat<R, N, S, kLoadPlain>(ublk, g.Vh, h);
-  Mat<R, N> w = mul_nd(u, st);
+  // W = U St^+: the heatbath forms it once and carries it along with U; the
+  // overrelaxation takes each subgroup's 2x2 block of it from the current U
+  // (or_block: 36 instead of about 41 complex products for SU(3); measured
+  // faster for overrelaxation only, 48^3 x 96: 0.479 -> 0.474 ms)
+  Mat<R, N> w;
+  if constexpr (MODE == kHeatbathMode) w = mul_nd(u, st);
 
   uint32_t step = 0;
   if constexpr (MODE == kHeatbathMode) step = *p.hb_step + p.step_offset;
@@ -421,8 +441,8 @@ __device__ __forceinline__ void pass_body(const PassParams& p, int par, int64_t 
   for (int i = 0; i < N - 1; ++i) {
 #pragma unroll
     for (int j = i + 1; j < N; ++j) {
-      const bool last = (i == N - 2) && (j == N - 1);
       if constexpr (MODE == kHeatbathMode) {
+        const bool last = (i == N - 2) && (j == N - 1);
         const Quat<R> v = block_to_quat(w.e[i][i], w.e[i][j], w.e[j][i], w.e[j][j]);
         const R k = d_sqrt(fma(v.a0, v.a0, fma(v.a1, v.a1, fma(v.a2, v.a2, v.a3 * v.a3))));
         if (k > R(1e-15) && d_isfinite(k)) {
@@ -438,14 +458,10 @@ __device__ __forceinline__ void pass_body(const PassParams& p, int par, int64_t 
         }
       } else {
         // v2 = 2v: |v2|^2 = 4 k^2, compared with 4 (1e-15)^2
-        const Quat<R> v2 = block_to_quat2(w.e[i][i], w.e[i][j], w.e[j][i], w.e[j][j]);
+        const Quat<R> v2 = or_block<R, N>(u, st, i, j);
         const R n3 = fma(v2.a1, v2.a1, fma(v2.a2, v2.a2, v2.a3 * v2.a3));
         const R k2 = fma(v2.a0, v2.a0, n3);
-        if (k2 > R(4e-30) && d_isfinite(k2)) {
-          const Quat<R> a = or_element(v2, n3, k2);
-          apply_rows(u, i, j, a);
-          if (!last) apply_rows(w, i, j, a);
-        }
+        if (k2 > R(4e-30) && d_isfinite(k2)) apply_rows(u, i, j, or_element(v2, n3, k2));
       }
       ++sub;
     }
@@ -1299,15 +1315,13 @@ __device__ __forceinline__ void or_pass_body2(const PassParams& p, int par, int6
 
   char* ublk = p.links + (2 * mu + par) * p.block_bytes;
   Mat<F2, N> u = load_mat2<N, S, kLoadPlain>(ublk, g.Vh, h0, h1);
-  Mat<F2, N> w = mul_nd(u, st);
 
 #pragma unroll
   for (int i = 0; i < N - 1; ++i) {
 #pragma unroll
     for (int j = i + 1; j < N; ++j) {
-      const bool last = (i == N - 2) && (j == N - 1);
-      // or_element of each lane, operation by operation (v2 = 2v)
-      const Quat<F2> v2 = block_to_quat2(w.e[i][i], w.e[i][j], w.e[j][i], w.e[j][j]);
+      // or_block and or_element of each lane, operation by operation (v2 = 2v)
+      const Quat<F2> v2 = or_block<F2, N>(u, st, i, j);
       const F2 n3 = fma(v2.a1, v2.a1, fma(v2.a2, v2.a2, v2.a3 * v2.a3));
       float k0, k1;
       f2_unpack(fma(v2.a0, v2.a0, n3), k0, k1);
@@ -1328,7 +1342,6 @@ __device__ __forceinline__ void or_pass_body2(const PassParams& p, int par, int6
         a.a3 = f2_pack(ok0 ? x0 : 0.0f, ok1 ? x1 : 0.0f);
       }
       apply_rows(u, i, j, a);
-      if (!last) apply_rows(w, i, j, a);
     }
   }
   if constexpr (REUNIT) {
