@@ -269,36 +269,47 @@ __device__ __forceinline__ void su3_third_row(Mat<R, 3>& m) {
 // GB300 converts between FP32 and FP64 at its FP64 rate: about 2 conversions a
 // clock per SM, the rate of its FP64 FMAs, against about 118 FP32 FMAs
 // (measured).  to_f64 and to_f32 do these conversions with integer operations on
-// the IEEE 754 binary32 and binary64 encodings (sign, biased exponent, fraction):
-// float -> double is exact (the fraction is extended by 29 zero bits and the
-// exponent rebiased from 127 to 1023); double -> float keeps the top 23 fraction
-// bits and rounds to nearest, ties to even, on the 29 bits dropped.  Operands the
-// integer path does not cover (subnormal, infinite or NaN floats; doubles whose
-// float is subnormal, infinite or NaN) take the hardware conversion, so both
-// functions return exactly the hardware's result for every operand
+// the IEEE 754 binary32 and binary64 encodings (sign, biased exponent, fraction),
+// and return exactly the hardware's result for every operand
 // (sun_selftest_conversions checks this bit for bit).
+//
+// float -> double is exact: the fraction is extended by 29 zero bits and the
+// exponent rebiased from 127 to 1023.  Every case is taken by selects, with no
+// branch: +-0 keeps exponent 0; a subnormal float m 2^-149 is normalised (its top
+// fraction bit p becomes the hidden bit, exponent p + 874); infinities keep a zero
+// fraction and NaNs their payload with the quiet bit set, as the hardware does.
+// A branch to the hardware conversion for the rare cases was if-converted by the
+// compiler, which then issued that conversion for every operand.
 __device__ __forceinline__ double to_f64(float f) {
   const uint32_t b = __float_as_uint(f);
   const uint32_t e = (b >> 23) & 0xffu;
-  if (e == 0xffu || (e == 0u && (b << 9) != 0u)) return double(f);
-  const uint32_t ed = e == 0u ? 0u : e + 896u;  // +-0 keeps exponent 0
-  const uint32_t hi = (b & 0x80000000u) | (ed << 20) | ((b >> 3) & 0x000fffffu);
-  return __hiloint2double(int(hi), int(b << 29));
+  const uint32_t m = b & 0x007fffffu;
+  const uint32_t p = 31u - uint32_t(__clz(m | 1u));  // top set bit of a subnormal's fraction
+  uint32_t ed = e == 0u ? (m == 0u ? 0u : p + 874u) : (e == 0xffu ? 0x7ffu : e + 896u);
+  uint32_t fr = e == 0u ? (m << (23u - p)) & 0x007fffffu : m;
+  fr = (e == 0xffu && m != 0u) ? (fr | 0x00400000u) : fr;
+  const uint32_t hi = (b & 0x80000000u) | (ed << 20) | (fr >> 3);
+  return __hiloint2double(int(hi), int(fr << 29));
 }
 __device__ __forceinline__ double to_f64(double d) { return d; }
 
+// double -> float keeps the top 23 fraction bits and rounds to nearest, ties to
+// even, on the 29 bits dropped (a carry out of the fraction raises the exponent,
+// 254 -> 255 being the overflow to infinity).  Doubles whose float is subnormal,
+// infinite or NaN go to the hardware conversion in a function of its own, so that
+// the common path issues no FP64-pipe instruction.
+static __device__ __noinline__ float to_f32_rare(double d) { return float(d); }
 __device__ __forceinline__ float to_f32(double d) {
   const uint32_t hi = uint32_t(__double2hiint(d)), lo = uint32_t(__double2loint(d));
   const uint32_t e = (hi >> 20) & 0x7ffu;
   if (e - 897u < 254u) {  // the float is normal before rounding: exponent e - 896 in [1, 254]
     uint32_t f = (hi & 0x80000000u) | ((e - 896u) << 23) | ((hi & 0x000fffffu) << 3) | (lo >> 29);
     const uint32_t rest = lo & 0x1fffffffu;
-    // a carry out of the fraction raises the exponent (254 -> 255 is the overflow to infinity)
     f += (rest > 0x10000000u || (rest == 0x10000000u && (f & 1u) != 0u)) ? 1u : 0u;
     return __uint_as_float(f);
   }
   if (((hi << 1) | lo) == 0u) return __uint_as_float(hi & 0x80000000u);  // +-0
-  return float(d);
+  return to_f32_rare(d);
 }
 __device__ __forceinline__ float to_f32(float f) { return f; }
 

@@ -232,11 +232,12 @@ __device__ __forceinline__ Mat<B, N> mat_cast(const Mat<A, N>& m) {
 }
 
 // mat_cast with the FP32 <-> FP64 conversions done on the integer pipe (to_f64,
-// to_f32: the same bits).  For the re-unitarization kernels, whose time is the
-// FP64 pipe's (measured, separate pass: SU(4) 32^4 4.19 -> 3.92 ms, SU(6) 24^4
-// 4.05 -> 3.92 ms).  Not in the update passes: there the hardware conversions
-// overlap the FP32 work, and the integer sequences cost issue slots (the fused
-// re-unitarizing step 6.46 -> 6.77 ms, the plaquette 0.75 -> 0.81 ms).
+// to_f32: the same bits).  For the re-unitarization kernels and the update
+// passes that re-unitarize, whose time is the FP64 pipe's (measured: the fused
+// SU(3) overrelaxation pass 0.807 -> 0.716 ms at 48^3 x 96, its FP64 pipe 83%
+// busy before; the separate pass, SU(4) 32^4 4.19 -> 3.92 ms, SU(6) 24^4 4.05 ->
+// 3.92 ms).  The plaquette, whose FP64 pipe is a third busy, keeps the hardware
+// conversions.
 template <class A, class B, int N>
 __device__ __forceinline__ Mat<B, N> mat_cast_int(const Mat<A, N>& m) {
   Mat<B, N> o;
@@ -468,9 +469,9 @@ __device__ __forceinline__ void pass_body(const PassParams& p, int par, int64_t 
   }
   if constexpr (REUNIT) {
     if (reunit_selected(p, glex >> 1)) {
-      Mat<double, N> d = mat_cast<R, double, N>(u);
+      Mat<double, N> d = mat_cast_int<R, double, N>(u);
       reunit_d<N>(d);
-      u = mat_cast<double, R, N>(d);
+      u = mat_cast_int<double, R, N>(d);
     }
   }
   store_mat<R, N, S>(ublk, g.Vh, h, u);
