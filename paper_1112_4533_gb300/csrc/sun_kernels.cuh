@@ -15,11 +15,13 @@ constexpr int kMaxBlockThreads = 256;
 // resident 128-thread blocks per SM the register-bounded kernels (variant bit 1)
 // are compiled for: 5 measured fastest among 4..8 for the SU(3) FP32 passes on
 // GB300 (more warps cost more spills than they hide latency); with the two-row
-// staple products (bit 2) the overrelaxation pass needs fewer registers and 6
-// blocks are faster (48^3 x 96: 0.533 -> 0.517 ms; its heatbath pass stays at 5)
+// staple products (bit 2) the overrelaxation passes need fewer registers and 7
+// blocks (72 registers) are fastest, for the fused re-unitarizing pass too
+// (48^3 x 96, against 6 blocks: 0.474 -> 0.467 ms, fused 0.709 -> 0.684 ms; 8
+// blocks: 0.472 ms); the heatbath pass stays at 5
 constexpr int kOccBlocks = 5;
-constexpr int kOccBlocksTwoRowOR = 6;  // 7 and 8 blocks measured no faster
-constexpr int kOccBlocksTwoRowHB = 5;  // 6 blocks: 0.722 -> 0.767 ms
+constexpr int kOccBlocksTwoRowOR = 7;
+constexpr int kOccBlocksTwoRowHB = 5;  // 6 blocks: 0.706 -> 0.743 ms
 // the same bound for the SU(4) FP32 per-link passes: 4 blocks (128 registers)
 constexpr int kOccBlocksSU4 = 4;
 template <int N, int VAR = 1, int MODE = 0>
@@ -105,7 +107,11 @@ __device__ __forceinline__ void apply_rows(Mat<R, N>& m, int i, int j, const Qua
 // term, 35 d^4 / 128, is below 4e-18 for |d| < 2^-14.  Other rows use rsqrt().
 __device__ __forceinline__ double rsqrt_near_one(double s) {
   const double d = s - 1.0;
-  if (fabs(d) < 0x1p-14) return fma(fma(fma(-0.3125, d, 0.375), d, -0.5), d, 1.0);
+  // |d| < 2^-14 read off the exponent bits: an integer compare instead of one on
+  // the FP64 pipe, which bounds the re-unitarizing passes (fused SU(3) pass at
+  // 48^3 x 96: 0.718 -> 0.709 ms)
+  if ((uint32_t(__double2hiint(d)) & 0x7ff00000u) < (uint32_t(1023 - 14) << 20))
+    return fma(fma(fma(-0.3125, d, 0.375), d, -0.5), d, 1.0);
   return rsqrt(s);
 }
 
