@@ -241,8 +241,8 @@ __device__ __forceinline__ Mat<B, N> mat_cast(const Mat<A, N>& m) {
 // to_f32: the same bits).  For the re-unitarization kernels and the update
 // passes that re-unitarize, whose time is the FP64 pipe's (measured: the fused
 // SU(3) overrelaxation pass 0.807 -> 0.716 ms at 48^3 x 96, its FP64 pipe 83%
-// busy before; the separate pass, SU(4) 32^4 4.19 -> 3.92 ms, SU(6) 24^4 4.05 ->
-// 3.92 ms).  The plaquette, whose FP64 pipe is a third busy, keeps the hardware
+// busy before; the separate pass, SU(4) 32^4 4.19 -> 3.63 ms, SU(6) 24^4 4.05 ->
+// 3.67 ms).  The plaquette, whose FP64 pipe is a third busy, keeps the hardware
 // conversions.
 template <class A, class B, int N>
 __device__ __forceinline__ Mat<B, N> mat_cast_int(const Mat<A, N>& m) {
